@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the WSM hot path on GB300.
+
+Workload (one step): 8 seeded 512x512 RGB images (noise amplitude swept
+0..24, 18k..229k unique colors each), K = 256, fixed-iteration WSM
+(10 iterations): for every image reduce -> init -> iterate -> map -> MSE.
+
+  value   unique-color assignments per second (sum over the images of
+          N' x iterations, divided by the step time), inputs resident in HBM;
+  e2e     the same metric through the public API from pinned host buffers,
+          with the host->device copy of the pixels and the device->host copy
+          of the index image, palette and MSE inside the timed region;
+  roofline  the persistent sort-means kernel (dominant): evaluated distances x
+          8 FLOP per launch over its CUDA-event duration, against the FP32
+          CUDA-core peak (SMs x 128 lanes x 2 FLOP x max SM clock);
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload.
+
+``--impl reference`` times the CPU oracle instead (the reference arm).
+Multi-GPU (torchrun): every rank quantizes its own 8 images (weak scaling,
+no collective on the data path); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+K_PALETTE = 256
+ITERS = 10
+N_IMAGES = 8
+H = W = 512
+METRIC = "unique-color assignments/s per iter (K=256) vs FP32 peak; 512² images/s end-to-end"
+UNIT = "assignments/s"
+L2_FLUSH_BYTES = 256 << 20
+KERNELS_PER_IMAGE = 9   # hist24, scan_count, scan_emit, init, sortmeans, sortmeans(map),
+#                         gather, mse_partial, mse_final
+
+
+def workload(rank: int):
+    """The rank's 8 images: seeds 1..8 (+8*rank), noise 0..24."""
+    return [synth.image(H, W, 8 * rank + s + 1, a) for s, a in enumerate(synth.SWEEP_NOISE)]
+
+
+def image_seed(rank: int, s: int) -> int:
+    return 1000 * (8 * rank + s) + K_PALETTE
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm and CPU baseline: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def oracle_sample(images, budget_s: float, start: int = 0):
+    """Run the oracle on whole images (cycling) until budget_s has elapsed."""
+    import oracle
+    oracle.build()
+    units, t0, n, s = 0, time.perf_counter(), 0, start
+    while True:
+        r = oracle.quantize(images[s % len(images)], K_PALETTE, image_seed(0, s % len(images)),
+                            ITERS, 0.0)
+        units += len(r["colors"]) * r["iters"]
+        n += 1
+        s += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            return units, el, n
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    images = workload(0)
+    oracle_sample(images, 0.0)                     # build + first touch
+    for w in range(args.warmup):
+        oracle_sample(images, 0.0, start=w)
+    units, secs, nimg = 0, 0.0, 0
+    for k in range(args.steps):
+        u, t, n = oracle_sample(images, 0.0, start=k)   # one image per step
+        units, secs, nimg = units + u, secs + t, nimg + n
+    value = units / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "sweep 8x512x512 noise 0..24, K=256, WSM 10 iterations",
+                   "sample": "one whole image per step, cycling through the 8"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{nimg} whole images (one per step), single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1011_0093_gb300 as wsm
+    from paper_1011_0093_gb300 import _native as nat
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    images = workload(rank)
+    n = H * W
+    d_imgs = [torch.from_numpy(im).to(dev) for im in images]
+    h_imgs = [torch.from_numpy(im).pin_memory() for im in images]
+    handle = wsm.Handle(K_PALETTE, n, n)
+    colors = [torch.empty(n, dtype=torch.uint32, device=dev) for _ in images]
+    counts = [torch.empty(n, dtype=torch.uint32, device=dev) for _ in images]
+    centers = [torch.empty((K_PALETTE, 4), dtype=torch.float32, device=dev) for _ in images]
+    labels = [torch.empty(n, dtype=torch.uint8, device=dev) for _ in images]
+    index = [torch.empty((H, W), dtype=torch.uint8, device=dev) for _ in images]
+    mse = torch.empty(len(images), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    it_events = []          # (start, end) around every persistent iterate launch
+    n_unique = [0] * len(images)
+
+    def step(record: bool):
+        for s, img in enumerate(d_imgs):
+            nu = wsm.wsm_reduce(handle, img, colors[s], counts[s])
+            n_unique[s] = nu
+            wsm.wsm_init(handle, colors[s], nu, K_PALETTE, image_seed(rank, s), centers[s],
+                         labels[s])
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            wsm.wsm_iterate(handle, colors[s], counts[s], nu, K_PALETTE, centers[s], labels[s],
+                            ITERS, 0.0, sync=False)
+            if record:
+                e1.record(stream)
+                it_events.append((s, e0, e1))
+            wsm.wsm_map(handle, img, colors[s], nu, centers[s], K_PALETTE, labels[s], index[s])
+            wsm.wsm_distortion(handle, img, centers[s], K_PALETTE, index[s], d_mse=mse[s:s + 1],
+                               sync=False)
+
+    # distances evaluated per image (deterministic: same inputs every step)
+    evaluated = []
+    for s in range(len(images)):
+        nu = wsm.wsm_reduce(handle, d_imgs[s], colors[s], counts[s])
+        wsm.wsm_init(handle, colors[s], nu, K_PALETTE, image_seed(rank, s), centers[s], labels[s])
+        done, _ = wsm.wsm_iterate(handle, colors[s], counts[s], nu, K_PALETTE, centers[s],
+                                  labels[s], ITERS, 0.0)
+        evaluated.append(wsm.wsm_iterate_stats(handle, K_PALETTE, sums=False)[0])
+    for _ in range(args.warmup):
+        step(False)
+    wsm.wsm_sync_status(handle)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)                                   # evict L2 between steps
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(True)
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+    barrier()
+    wsm.wsm_sync_status(handle)
+    units_step = sum(n_unique) * ITERS
+    total_ms = sum(step_ms)
+
+    # e2e through the public API from pinned host memory
+    e2e_ms = []
+    h2d = sum(im.numel() for im in h_imgs)
+    d2h = len(images) * (n + K_PALETTE * 16 + 8)
+    out_idx = [torch.empty((H, W), dtype=torch.uint8).pin_memory() for _ in images]
+    out_pal = [torch.empty((K_PALETTE, 4), dtype=torch.float32).pin_memory() for _ in images]
+    out_mse = torch.empty(len(images), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        for s, himg in enumerate(h_imgs):
+            img = himg.to(dev, non_blocking=True)
+            q = wsm.quantize(img, K_PALETTE, seed=image_seed(rank, s), max_iter=ITERS, eps=0.0,
+                             handle=handle, mse=False)
+            wsm.wsm_distortion(handle, img, q.centers, K_PALETTE, q.index, d_mse=mse[s:s + 1],
+                               sync=False)
+            out_idx[s].copy_(q.index, non_blocking=True)
+            out_pal[s].copy_(q.centers, non_blocking=True)
+        out_mse.copy_(mse, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(max(args.warmup, 1)):
+        e2e_step()
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    barrier()
+    clk = clocks.stop()
+
+    # roofline of the persistent sort-means kernel, from the timed steps
+    it_ms = [e0.elapsed_time(e1) for _, e0, e1 in it_events]
+    it_flop = [8.0 * evaluated[s] for s, _, _ in it_events]
+    achieved_tflops = sum(it_flop) / (sum(it_ms) * 1e-3) / 1e12
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+    t_max = torch.tensor([total_ms, sum(e2e_ms)], dtype=torch.float64, device=dev)
+    units = torch.tensor([float(units_step)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(units, op=dist.ReduceOp.SUM)
+    total_ms, e2e_total = float(t_max[0]), float(t_max[1])
+    all_units = float(units[0])
+    value = all_units * args.steps / (total_ms * 1e-3)
+    e2e_value = all_units * args.steps / (e2e_total * 1e-3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        u, secs, nimg = oracle_sample(images, args.cpu_seconds)
+        cpu = {"value": u / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nimg} whole 512x512 images of the same sweep (K=256, 10 iterations),"
+                         f" single thread, {secs:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "sweep 8x512x512 noise 0..24 per GPU, K=256, WSM 10 iterations",
+                       "unique_colors": n_unique, "images_per_step": len(images) * world,
+                       "images_per_s": len(images) * world * args.steps / (total_ms * 1e-3),
+                       "images_per_s_e2e": len(images) * world * args.steps / (e2e_total * 1e-3),
+                       "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "alu", "kernel": "k_sortmeans<iterate>",
+                         "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / fp32_peak, "traffic": None,
+                         "peak_kind": f"FP32 {sms} SMs x 128 x 2 x {pk.get('sm_max_mhz')} MHz "
+                                      f"({pk_kind} max clock)",
+                         "launch_ms": sum(it_ms) / len(it_ms),
+                         "flop_per_launch": sum(it_flop) / len(it_flop)},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": KERNELS_PER_IMAGE * len(images) * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    handle.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wsm", choices=["wsm", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

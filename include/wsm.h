@@ -1,0 +1,188 @@
+/*
+ * wsm.h -- C ABI of libwsm, a GB300 (sm_103a) implementation of Weighted
+ * Sort-Means (WSM) color quantization (M. E. Celebi, "Fast Color
+ * Quantization Using Weighted Sort-Means Clustering", arXiv:1011.0093).
+ *
+ * Problem (Sec. 1): an image of N pixels of 24-bit RGB is reduced to a
+ * palette of K colors plus an index image.  The path is
+ *   wsm_reduce      unique colors and their frequencies   (Sec. 2, data
+ *                   sampling and sample weighting)
+ *   wsm_init        K random unique colors as centers     (Algorithm 2,
+ *                   first step; Sec. 3.2 random initialisation)
+ *   wsm_iterate     the Sort-Means loop with weighted means and the
+ *                   termination rule                      (Algorithm 2,
+ *                   Sec. 3.2)
+ *   wsm_map         final assignment and pixel mapping    (Sec. 1)
+ *   wsm_distortion  mean squared error of the mapping     (Sec. 3.1, Eq. 2)
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: WSM_OK (0) or a negative
+ *     WSM_E_* code.  No function aborts the process.  wsm_last_error()
+ *     returns a message for the calling thread's last failure.
+ *   - Pointers named d_* are device pointers to memory owned by the caller;
+ *     the library never frees them and keeps no reference after a call
+ *     returns.  Pointers without the prefix are host pointers.
+ *   - A wsm_handle owns library scratch memory on the device that was
+ *     current at wsm_create; every later call on it must run with that
+ *     device current.  One handle serves one stream at a time: calls that
+ *     share a handle must be ordered on the same stream (or synchronised).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *     are asynchronous on it unless they return a host value (documented
+ *     per function), in which case they synchronise the stream.
+ *   - Kernel-side failures (a grid barrier that waited too long, a label or
+ *     palette index >= K in the input, more unique colors than the output
+ *     can hold) are recorded in a per-handle status word; the next call that
+ *     synchronises reports them (WSM_E_TIMEOUT, WSM_E_INVAL, WSM_E_CAPACITY)
+ *     and clears the word.  wsm_sync_status() does so explicitly.
+ *
+ * Data layouts:
+ *   pixels   uint8 [N][pixel_stride], pixel_stride 3 (R,G,B) or 4 (R,G,B,x;
+ *            the fourth byte is ignored).
+ *   colors   uint32 [N'] packed 0x00RRGGBB, strictly ascending.
+ *   counts   uint32 [N'] pixel frequency of each color (w_i = n_i / N).
+ *   centers  float32 [K][4] = (R, G, B, unused), the palette c_1..c_K.
+ *   labels   uint8 [N'] membership m[i] in [0, K) of each unique color.
+ *   index    uint8 [N] palette index of each pixel.
+ * Limits: 1 <= K <= 256 (uint8 labels); N <= 2^24 pixels per image, which
+ * keeps every per-cluster sum of n_i * x_i below 2^32.
+ */
+#ifndef WSM_H
+#define WSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define WSM_API __attribute__((visibility("default")))
+#else
+#define WSM_API
+#endif
+
+typedef struct wsm_handle wsm_handle;
+typedef struct CUstream_st* wsm_stream; /* same type as cudaStream_t */
+
+enum {
+    WSM_OK = 0,
+    WSM_E_INVAL = -1,    /* bad argument, or a label / index >= K found on the device */
+    WSM_E_NOMEM = -2,    /* device or host allocation failed */
+    WSM_E_CUDA = -3,     /* a CUDA runtime call failed; see wsm_last_error() */
+    WSM_E_TIMEOUT = -4,  /* a device-side wait gave up (bounded spin) */
+    WSM_E_STATE = -5,    /* handle used on the wrong device, or destroyed */
+    WSM_E_CAPACITY = -6  /* more unique colors than the output arrays hold */
+};
+
+#define WSM_MAX_K 256
+#define WSM_MAX_PIXELS (1ll << 24)
+
+/* Message describing the calling thread's most recent failure ("" if none).
+ * The string stays valid until the thread's next libwsm call. */
+WSM_API const char* wsm_last_error(void);
+
+/* Create a handle for images of at most max_pixels pixels, at most
+ * max_unique unique colors and palettes of at most max_K colors, on the
+ * current device.  Allocates the scratch: a 2^24-bin uint32 color histogram
+ * (64 MiB) with a one-bit-per-bin occupancy map (2 MiB), a 2^24-entry uint8
+ * color->label table (16 MiB), the max_K x max_K sorted center tables and
+ * the reduction and barrier words.  Errors: WSM_E_INVAL (limits out of
+ * range), WSM_E_NOMEM, WSM_E_CUDA.  *h is NULL on failure. */
+WSM_API int wsm_create(wsm_handle** h, int max_K, int64_t max_pixels, int64_t max_unique);
+
+/* Free the handle and its scratch (synchronises the device first).
+ * NULL is accepted. */
+WSM_API int wsm_destroy(wsm_handle* h);
+
+/* Read, report and clear the handle's device status word (synchronises
+ * `stream`).  Returns WSM_OK if no kernel-side failure was recorded. */
+WSM_API int wsm_sync_status(wsm_handle* h, wsm_stream stream);
+
+/* Sec. 2, data sampling + sample weighting.  The unique colors of the
+ * image and their pixel counts: d_colors[0..N') ascending, d_counts[i] the
+ * number of pixels of color d_colors[i].  The paper uses a chained hash
+ * table; this builds a 2^24-bin count histogram with warp-aggregated atomics
+ * and compacts it with a prefix scan over the occupancy map, which yields
+ * the same set already in ascending order, and leaves the histogram zeroed
+ * for the next image.
+ *   d_rgb        [n_pixels][pixel_stride] uint8, 0 <= n_pixels <= max_pixels
+ *   d_colors,
+ *   d_counts     [capacity] each; capacity >= N' or WSM_E_CAPACITY
+ *   d_n_unique   device int64, receives N' (may be NULL)
+ *   n_unique     host int64, receives N' (may be NULL; if given, the call
+ *                synchronises `stream`; otherwise it is asynchronous)
+ * Errors: WSM_E_INVAL (sizes, stride), WSM_E_CAPACITY (N' > capacity: the
+ * first `capacity` colors are written, the histogram is still cleared). */
+WSM_API int wsm_reduce(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, int pixel_stride,
+               uint32_t* d_colors, uint32_t* d_counts, int64_t capacity,
+               int64_t* d_n_unique, int64_t* n_unique, wsm_stream stream);
+
+/* Algorithm 2, first step: the initial centers are K distinct unique
+ * colors chosen at random (Sec. 3.2 uses random initialisation).  The
+ * indices are drawn on the host with Floyd's sampling algorithm (Bentley &
+ * Floyd 1987) from the counter-based splitmix64 stream of `seed` (draw r =
+ * mix(seed + (r+1) * 0x9E3779B97F4A7C15), Steele et al. 2014; draw r picks
+ * t uniformly in [0, j] by t = draw mod (j+1)), sorted ascending, and
+ * gathered on the device: d_centers[k] = unpack(d_colors[idx_k]).  Every
+ * membership starts at 0: d_labels[i] = 0.  Asynchronous.
+ *   d_colors   [n_unique]; d_centers [K][4] out; d_labels [n_unique] out
+ * Errors: WSM_E_INVAL (K < 1, K > max_K, K > n_unique). */
+WSM_API int wsm_init(wsm_handle* h, const uint32_t* d_colors, int64_t n_unique, int K, uint64_t seed,
+             float* d_centers, uint8_t* d_labels, wsm_stream stream);
+
+/* Algorithm 2 with the Sec. 3.2 termination rule, in one persistent
+ * cooperative launch.  Each iteration: the K x K squared center distances
+ * d[p][j] and, per row p, the centers sorted by (d[p][j], j != p, j); then
+ * the pruned nearest-center search of every unique color starting from its
+ * previous membership p, which stops at the first center t of row p with
+ * d[p][t] >= 4 ||x_i - c_p||^2 and moves to a visited center when its
+ * distance is <= the running minimum; then the weighted means
+ * c_k = sum n_i x_i / sum n_i over m[i] = k, with exact integer sums and an
+ * empty cluster keeping its center.  SSE_i = sum_i (n_i / N) min_dist_i is
+ * taken in the assignment step of iteration i.
+ *   max_iter   >= 0 iterations at most
+ *   eps        > 0: WSM-C, stop after iteration i >= 2 once
+ *              (SSE_{i-1} - SSE_i) / SSE_i <= eps, or when SSE_i = 0;
+ *              <= 0: WSM, exactly max_iter iterations
+ *   d_centers  [K][4] in: current centers, out: centers after the last update
+ *   d_labels   [n_unique] in: memberships (each < K), out: the last assignment
+ *   iters_done host int (may be NULL), sse_trace host double [max_iter]
+ *              (may be NULL); if either is given the call synchronises.
+ * Distances are FP32 on CUDA cores in difference form; sums are integers.
+ * Errors: WSM_E_INVAL (K, sizes; label >= K found), WSM_E_TIMEOUT. */
+WSM_API int wsm_iterate(wsm_handle* h, const uint32_t* d_colors, const uint32_t* d_counts,
+                int64_t n_unique, int K, float* d_centers, uint8_t* d_labels, int max_iter,
+                double eps, int* iters_done, double* sse_trace, wsm_stream stream);
+
+/* Diagnostics of the last wsm_iterate on this handle, valid until the next
+ * wsm_iterate or wsm_map on it (synchronises):
+ * evaluated = number of distances ||x_i - c_k||^2 computed, summed over all
+ * colors and iterations (one per color for the previous center plus one per
+ * visited center); S [K][3] and W [K] (may be NULL) = the integer sums
+ * sum n_i x_i and sum n_i of the last update. */
+WSM_API int wsm_iterate_stats(wsm_handle* h, int K, int64_t* evaluated, int64_t* S, int64_t* W,
+                      wsm_stream stream);
+
+/* Sec. 1, pixel mapping.  One more pruned assignment of the unique colors
+ * against d_centers (starting from d_labels, which it updates), a scatter
+ * of the memberships into the handle's 2^24-entry color->label table, and
+ * a gather d_index[p] = table[color of pixel p].  d_colors must be the
+ * unique colors of these same pixels.  Asynchronous.
+ * Errors: WSM_E_INVAL (sizes, K; label >= K found), WSM_E_TIMEOUT. */
+WSM_API int wsm_map(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, int pixel_stride,
+            const uint32_t* d_colors, int64_t n_unique, const float* d_centers, int K,
+            uint8_t* d_labels, uint8_t* d_index, wsm_stream stream);
+
+/* Sec. 3.1, Eq. 2: MSE = (1/N) sum_p ||x_p - c_{index_p}||^2 over the three
+ * channels, accumulated in FP64 in a fixed order (deterministic).
+ *   d_mse  device double (may be NULL); mse host double (may be NULL; if
+ *          given, the call synchronises).
+ * Errors: WSM_E_INVAL (sizes, K; index >= K found). */
+WSM_API int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, int pixel_stride,
+                   const float* d_centers, int K, const uint8_t* d_index, double* d_mse,
+                   double* mse, wsm_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WSM_H */

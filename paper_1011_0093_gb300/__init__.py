@@ -1,0 +1,16 @@
+"""GB300-native Weighted Sort-Means (WSM) color quantization.
+
+Implements the method of M. E. Celebi, "Fast Color Quantization Using
+Weighted Sort-Means Clustering" (arXiv:1011.0093) as hand-written CUDA for
+sm_103a behind the C ABI of include/wsm.h (libwsm.so).  This package is the
+thin Python layer above it: ``_native`` marshals arguments to the C entry
+points, ``quantize`` chains them for one image.  PyTorch only provides device
+memory and streams.
+"""
+from ._native import (MAX_K, MAX_PIXELS, Handle, WsmError, lib, wsm_distortion, wsm_init,
+                      wsm_iterate, wsm_iterate_stats, wsm_map, wsm_reduce, wsm_sync_status)
+from .quantize import Quantized, quantize
+
+__all__ = ["MAX_K", "MAX_PIXELS", "Handle", "WsmError", "lib", "wsm_reduce", "wsm_init",
+           "wsm_iterate", "wsm_iterate_stats", "wsm_map", "wsm_distortion", "wsm_sync_status",
+           "Quantized", "quantize"]

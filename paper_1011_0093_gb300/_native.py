@@ -1,0 +1,210 @@
+"""ctypes binding of libwsm (include/wsm.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls, checks the
+tensors it is given (device, dtype, contiguity, size), passes their device
+pointers and the current CUDA stream, and turns a non-zero status into a
+WsmError.  All computation happens in the library's CUDA kernels; there is
+no other code path.  If libwsm.so has not been built, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwsm.so")
+
+WSM_OK = 0
+ERRORS = {-1: "WSM_E_INVAL", -2: "WSM_E_NOMEM", -3: "WSM_E_CUDA", -4: "WSM_E_TIMEOUT",
+          -5: "WSM_E_STATE", -6: "WSM_E_CAPACITY"}
+MAX_K = 256
+MAX_PIXELS = 1 << 24
+
+_lock = threading.Lock()
+_lib = None
+_P = C.c_void_p
+_I64 = C.c_int64
+
+SIGNATURES = {
+    "wsm_last_error": (C.c_char_p, []),
+    "wsm_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _I64, _I64]),
+    "wsm_destroy": (C.c_int, [_P]),
+    "wsm_sync_status": (C.c_int, [_P, _P]),
+    "wsm_reduce": (C.c_int, [_P, _P, _I64, C.c_int, _P, _P, _I64, _P, C.POINTER(_I64), _P]),
+    "wsm_init": (C.c_int, [_P, _P, _I64, C.c_int, C.c_uint64, _P, _P, _P]),
+    "wsm_iterate": (C.c_int, [_P, _P, _P, _I64, C.c_int, _P, _P, C.c_int, C.c_double,
+                              C.POINTER(C.c_int), _P, _P]),
+    "wsm_iterate_stats": (C.c_int, [_P, C.c_int, C.POINTER(_I64), _P, _P, _P]),
+    "wsm_map": (C.c_int, [_P, _P, _I64, C.c_int, _P, _I64, _P, C.c_int, _P, _P, _P]),
+    "wsm_distortion": (C.c_int, [_P, _P, _I64, C.c_int, _P, C.c_int, _P, _P,
+                                 C.POINTER(C.c_double), _P]),
+}
+
+
+class WsmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib():
+    """The loaded libwsm (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"libwsm.so not found at {LIB_PATH}: build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'`")
+            so = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(so, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = so
+    return _lib
+
+
+def _check(rc: int):
+    if rc != WSM_OK:
+        raise WsmError(rc, lib().wsm_last_error().decode(errors="replace"))
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream or None
+
+
+def _dev(t: torch.Tensor | None, dtype, name: str, min_numel: int = 0) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {min_numel}")
+    return t.data_ptr()
+
+
+def _pixels(rgb: torch.Tensor) -> tuple[int, int]:
+    stride = rgb.shape[-1]
+    if stride not in (3, 4):
+        raise ValueError("pixels must have 3 or 4 channels in the last dimension")
+    return rgb.numel() // stride, stride
+
+
+class Handle:
+    """Owns a wsm_handle (library scratch on the current device)."""
+
+    def __init__(self, max_K: int, max_pixels: int, max_unique: int | None = None):
+        h = C.c_void_p()
+        _check(lib().wsm_create(C.byref(h), int(max_K), int(max_pixels),
+                                int(max_unique if max_unique is not None else max_pixels)))
+        self.ptr = h.value
+        self.max_K = int(max_K)
+        self.max_pixels = int(max_pixels)
+        self.max_unique = int(max_unique if max_unique is not None else max_pixels)
+
+    def close(self):
+        if self.ptr:
+            lib().wsm_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def wsm_sync_status(h: Handle, stream=None):
+    _check(lib().wsm_sync_status(h.ptr, _stream(stream)))
+
+
+def wsm_reduce(h: Handle, rgb: torch.Tensor, colors: torch.Tensor, counts: torch.Tensor,
+               d_n_unique: torch.Tensor | None = None, sync: bool = True, stream=None):
+    """Unique colors + counts; returns N' (host int) if sync, else None."""
+    n, stride = _pixels(rgb)
+    cap = min(colors.numel(), counts.numel())
+    nu = _I64(0)
+    _check(lib().wsm_reduce(h.ptr, _dev(rgb, torch.uint8, "rgb"), n, stride,
+                            _dev(colors, torch.uint32, "colors"),
+                            _dev(counts, torch.uint32, "counts"), cap,
+                            _dev(d_n_unique, torch.int64, "d_n_unique", 1),
+                            C.byref(nu) if sync else None, _stream(stream)))
+    return int(nu.value) if sync else None
+
+
+def wsm_init(h: Handle, colors: torch.Tensor, n_unique: int, K: int, seed: int,
+             centers: torch.Tensor, labels: torch.Tensor, stream=None):
+    _check(lib().wsm_init(h.ptr, _dev(colors, torch.uint32, "colors", n_unique), n_unique, K,
+                          seed & (2 ** 64 - 1), _dev(centers, torch.float32, "centers", 4 * K),
+                          _dev(labels, torch.uint8, "labels", n_unique), _stream(stream)))
+
+
+def wsm_iterate(h: Handle, colors: torch.Tensor, counts: torch.Tensor, n_unique: int, K: int,
+                centers: torch.Tensor, labels: torch.Tensor, max_iter: int, eps: float,
+                sync: bool = True, stream=None):
+    """Returns (iterations done, SSE trace list) if sync, else None."""
+    it = C.c_int(0)
+    trace = (C.c_double * max(max_iter, 1))()
+    _check(lib().wsm_iterate(h.ptr, _dev(colors, torch.uint32, "colors", n_unique),
+                             _dev(counts, torch.uint32, "counts", n_unique), n_unique, K,
+                             _dev(centers, torch.float32, "centers", 4 * K),
+                             _dev(labels, torch.uint8, "labels", n_unique), max_iter, float(eps),
+                             C.byref(it) if sync else None,
+                             C.cast(trace, C.c_void_p) if sync else None, _stream(stream)))
+    if not sync:
+        return None
+    return it.value, [trace[i] for i in range(min(it.value, max_iter))]
+
+
+def wsm_iterate_stats(h: Handle, K: int, sums: bool = True, stream=None):
+    """(evaluated distances, S [K,3] int64 or None, W [K] int64 or None)."""
+    ev = _I64(0)
+    S = (_I64 * (3 * K))()
+    W = (_I64 * K)()
+    _check(lib().wsm_iterate_stats(h.ptr, K, C.byref(ev), C.cast(S, C.c_void_p) if sums else None,
+                                   C.cast(W, C.c_void_p) if sums else None, _stream(stream)))
+    if not sums:
+        return ev.value, None, None
+    return (ev.value, torch.tensor(list(S), dtype=torch.int64).view(K, 3),
+            torch.tensor(list(W), dtype=torch.int64))
+
+
+def wsm_map(h: Handle, rgb: torch.Tensor, colors: torch.Tensor, n_unique: int,
+            centers: torch.Tensor, K: int, labels: torch.Tensor, index: torch.Tensor,
+            stream=None):
+    n, stride = _pixels(rgb)
+    _check(lib().wsm_map(h.ptr, _dev(rgb, torch.uint8, "rgb"), n, stride,
+                         _dev(colors, torch.uint32, "colors", n_unique), n_unique,
+                         _dev(centers, torch.float32, "centers", 4 * K), K,
+                         _dev(labels, torch.uint8, "labels", n_unique),
+                         _dev(index, torch.uint8, "index", n), _stream(stream)))
+
+
+def wsm_distortion(h: Handle, rgb: torch.Tensor, centers: torch.Tensor, K: int,
+                   index: torch.Tensor, d_mse: torch.Tensor | None = None, sync: bool = True,
+                   stream=None):
+    """MSE of Eq. 2; returns the host float if sync, else None."""
+    n, stride = _pixels(rgb)
+    m = C.c_double(0.0)
+    _check(lib().wsm_distortion(h.ptr, _dev(rgb, torch.uint8, "rgb"), n, stride,
+                                _dev(centers, torch.float32, "centers", 4 * K), K,
+                                _dev(index, torch.uint8, "index", n),
+                                _dev(d_mse, torch.float64, "d_mse", 1),
+                                C.byref(m) if sync else None, _stream(stream)))
+    return m.value if sync else None

@@ -1,0 +1,212 @@
+// wsm_api.cu -- handle lifetime, error reporting, the status word, and the
+// initialisation step (Algorithm 2, first step; Sec. 3.2).
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "wsm_internal.cuh"
+
+namespace wsm {
+
+static thread_local std::string t_last_error;
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+    t_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(WSM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int check_handle(wsm_handle* h) {
+    if (!h) return fail(WSM_E_INVAL, "null handle");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != h->device)
+        return fail(WSM_E_STATE, "handle belongs to device " + std::to_string(h->device) +
+                                     " but device " + std::to_string(dev) + " is current");
+    return WSM_OK;
+}
+
+// Synchronise the stream, fetch the status word, clear it, and map it to a
+// return code.
+int read_status(wsm_handle* h, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(&h->host_ctrl->status, &h->ctrl->status, sizeof(unsigned),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&h->ctrl->status, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    unsigned st = h->host_ctrl->status;
+    if (st & ST_TIMEOUT) return fail(WSM_E_TIMEOUT, "a device-side grid barrier timed out");
+    if (st & ST_CAPACITY)
+        return fail(WSM_E_CAPACITY, "more unique colors than the output capacity");
+    if (st & ST_BAD_LABEL) return fail(WSM_E_INVAL, "a membership or palette index was >= K");
+    return WSM_OK;
+}
+
+// splitmix64 (Steele, Lea, Flood 2014): draw r of the stream seeded with
+// `seed` is the state seed + (r+1) * golden-gamma passed through the mixer.
+static uint64_t splitmix_draw(uint64_t seed, uint64_t r) {
+    uint64_t s = seed + 0x9E3779B97F4A7C15ull * (r + 1ull);
+    s ^= s >> 30;
+    s *= 0xBF58476D1CE4E5B9ull;
+    s ^= s >> 27;
+    s *= 0x94D049BB133111EBull;
+    s ^= s >> 31;
+    return s;
+}
+
+// Floyd's sampling (Bentley & Floyd, "A sample of brilliance", CACM 1987):
+// K distinct integers from [0, n), each K-subset equally likely; returned
+// in ascending order.
+static std::vector<int64_t> floyd_sample(int64_t n, int K, uint64_t seed) {
+    std::vector<int64_t> pick;
+    pick.reserve(K);
+    uint64_t r = 0;
+    for (int64_t top = n - K; top < n; ++top) {
+        int64_t t = (int64_t)(splitmix_draw(seed, r++) % (uint64_t)(top + 1));
+        bool seen = std::find(pick.begin(), pick.end(), t) != pick.end();
+        pick.push_back(seen ? top : t);
+    }
+    std::sort(pick.begin(), pick.end());
+    return pick;
+}
+
+struct InitPick {
+    uint32_t idx[WSM_MAX_K];
+};
+
+__global__ void k_init(const uint32_t* __restrict__ colors, int64_t n_unique, int K, InitPick pick,
+                       float4* __restrict__ centers, uint8_t* __restrict__ labels) {
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid < K) {
+        uint32_t c = colors[pick.idx[tid]];
+        centers[tid] = make_float4((float)((c >> 16) & 255u), (float)((c >> 8) & 255u),
+                                   (float)(c & 255u), 0.f);
+    }
+    for (int64_t i = tid; i < n_unique; i += (int64_t)gridDim.x * blockDim.x) labels[i] = 0;
+}
+
+int iterate_kernel_setup(wsm_handle* h);   // wsm_iterate.cu
+
+}  // namespace wsm
+
+using namespace wsm;
+
+extern "C" const char* wsm_last_error(void) { return t_last_error.c_str(); }
+
+extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64_t max_unique) {
+    if (!out) return fail(WSM_E_INVAL, "null output pointer");
+    *out = nullptr;
+    if (max_K < 1 || max_K > WSM_MAX_K) return fail(WSM_E_INVAL, "max_K must be in [1, 256]");
+    if (max_pixels < 1 || max_pixels > WSM_MAX_PIXELS)
+        return fail(WSM_E_INVAL, "max_pixels must be in [1, 2^24]");
+    if (max_unique < 1 || max_unique > max_pixels)
+        return fail(WSM_E_INVAL, "max_unique must be in [1, max_pixels]");
+    wsm_handle* h = new (std::nothrow) wsm_handle();
+    if (!h) return fail(WSM_E_NOMEM, "host allocation failed");
+    h->max_K = max_K;
+    h->max_pixels = max_pixels;
+    h->max_unique = max_unique;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount,
+                                                      h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "device query");
+    }
+    int rc = iterate_kernel_setup(h);
+    if (rc != WSM_OK) {
+        delete h;
+        return rc;
+    }
+    size_t kk = (size_t)max_K * max_K;
+    struct {
+        void** p;
+        size_t bytes;
+    } allocs[] = {
+        {(void**)&h->hist, sizeof(uint32_t) * kHistBins},
+        {(void**)&h->bitmap, sizeof(uint32_t) * kMapWords},
+        {(void**)&h->blk_total, sizeof(uint32_t) * kScanBlocks},
+        {(void**)&h->lut, (size_t)kHistBins},
+        {(void**)&h->tab, sizeof(float4) * kk},
+        {(void**)&h->tab_nb, kk},
+        {(void**)&h->acc, sizeof(unsigned long long) * 2 * 4 * max_K},
+        {(void**)&h->sse_part, sizeof(double) * 2 * h->iter_grid},
+        {(void**)&h->trace, sizeof(double) * kMaxTrace},
+        {(void**)&h->mse_part, sizeof(double) * 1032},   // 1024 partials + result
+        {(void**)&h->ctrl, sizeof(Ctrl)},
+    };
+    for (auto& a : allocs) {
+        e = cudaMalloc(a.p, a.bytes);
+        if (e != cudaSuccess) {
+            wsm_destroy(h);
+            return fail(WSM_E_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+    }
+    e = cudaMallocHost((void**)&h->host_ctrl, sizeof(Ctrl));
+    if (e != cudaSuccess) {
+        wsm_destroy(h);
+        return fail(WSM_E_NOMEM, "cudaMallocHost failed");
+    }
+    e = cudaMemset(h->hist, 0, sizeof(uint32_t) * kHistBins);
+    if (e == cudaSuccess) e = cudaMemset(h->bitmap, 0, sizeof(uint32_t) * kMapWords);
+    if (e == cudaSuccess) e = cudaMemset(h->ctrl, 0, sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaMemset(h->acc, 0, sizeof(unsigned long long) * 8 * max_K);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        wsm_destroy(h);
+        return cuda_fail(e, "scratch initialisation");
+    }
+    *out = h;
+    return WSM_OK;
+}
+
+extern "C" int wsm_destroy(wsm_handle* h) {
+    if (!h) return WSM_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (h->device >= 0 && prev != h->device) cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    void* dev_ptrs[] = {h->hist, h->bitmap, h->blk_total, h->lut, h->tab, h->tab_nb,
+                        h->acc, h->sse_part, h->trace, h->mse_part, h->ctrl};
+    for (void* p : dev_ptrs)
+        if (p) cudaFree(p);
+    if (h->host_ctrl) cudaFreeHost(h->host_ctrl);
+    if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+    delete h;
+    return WSM_OK;
+}
+
+extern "C" int wsm_sync_status(wsm_handle* h, wsm_stream stream) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    return read_status(h, (cudaStream_t)stream);
+}
+
+extern "C" int wsm_init(wsm_handle* h, const uint32_t* d_colors, int64_t n_unique, int K,
+                        uint64_t seed, float* d_centers, uint8_t* d_labels, wsm_stream stream) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (K < 1 || K > h->max_K) return fail(WSM_E_INVAL, "K out of [1, max_K]");
+    if (n_unique < K || n_unique > h->max_unique)
+        return fail(WSM_E_INVAL, "n_unique must be in [K, max_unique]");
+    if (!d_colors || !d_centers || !d_labels) return fail(WSM_E_INVAL, "null device pointer");
+    std::vector<int64_t> pick = floyd_sample(n_unique, K, seed);
+    InitPick p;
+    for (int k = 0; k < K; ++k) p.idx[k] = (uint32_t)pick[k];
+    int threads = 256;
+    int64_t want = (n_unique + threads - 1) / threads;
+    int blocks = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)h->sms * 8);
+    k_init<<<blocks, threads, 0, (cudaStream_t)stream>>>(d_colors, n_unique, K, p,
+                                                          (float4*)d_centers, d_labels);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_init launch");
+    return WSM_OK;
+}

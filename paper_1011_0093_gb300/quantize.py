@@ -1,0 +1,53 @@
+"""One image through the whole path: reduce -> init -> iterate -> map -> MSE.
+
+Only allocation (torch) and the sequence of C-ABI calls live here.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import _native as N
+
+
+@dataclass
+class Quantized:
+    centers: torch.Tensor     # float32 [K, 4] palette (R, G, B, unused), device
+    index: torch.Tensor       # uint8 [H, W] palette index per pixel, device
+    colors: torch.Tensor      # uint32 [N'] unique colors, device
+    counts: torch.Tensor      # uint32 [N'] pixel counts, device
+    labels: torch.Tensor      # uint8 [N'] final membership of each unique color, device
+    n_unique: int
+    iters: int
+    sse_trace: list
+    mse: float | None
+
+
+def quantize(rgb: torch.Tensor, K: int, seed: int = 0, max_iter: int = 10, eps: float = 0.0,
+             handle: N.Handle | None = None, mse: bool = True, stream=None) -> Quantized:
+    """Quantize one uint8 [H, W, 3|4] CUDA image to K colors.
+
+    eps <= 0 runs exactly max_iter iterations (WSM); eps > 0 stops on the
+    relative SSE change (WSM-C, Sec. 3.2) or at max_iter.
+    """
+    if not rgb.is_cuda or rgb.dtype != torch.uint8 or rgb.dim() != 3:
+        raise ValueError("rgb must be a uint8 CUDA tensor of shape [H, W, 3|4]")
+    rgb = rgb.contiguous()
+    H, W, _ = rgb.shape
+    n = H * W
+    h = handle if handle is not None else N.Handle(max(K, 1), n, n)
+    dev = rgb.device
+    colors = torch.empty(n, dtype=torch.uint32, device=dev)
+    counts = torch.empty(n, dtype=torch.uint32, device=dev)
+    nu = N.wsm_reduce(h, rgb, colors, counts, stream=stream)
+    colors, counts = colors[:nu], counts[:nu]
+    centers = torch.empty((K, 4), dtype=torch.float32, device=dev)
+    labels = torch.empty(nu, dtype=torch.uint8, device=dev)
+    N.wsm_init(h, colors, nu, K, seed, centers, labels, stream=stream)
+    iters, trace = N.wsm_iterate(h, colors, counts, nu, K, centers, labels, max_iter, eps,
+                                 stream=stream)
+    index = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    N.wsm_map(h, rgb, colors, nu, centers, K, labels, index, stream=stream)
+    m = N.wsm_distortion(h, rgb, centers, K, index, stream=stream) if mse else None
+    return Quantized(centers, index, colors, counts, labels, nu, iters, trace, m)
