@@ -163,6 +163,33 @@ WSM_API int wsm_iterate(wsm_handle* h, const uint32_t* d_colors, const uint32_t*
 WSM_API int wsm_iterate_stats(wsm_handle* h, int K, int64_t* evaluated, int64_t* S, int64_t* W,
                       wsm_stream stream);
 
+/* Allocation-free variant of wsm_iterate.  The paper has no counterpart:
+ * it exists for callers that cannot call cudaMalloc -- a plugin inside a
+ * host program that owns every device byte through its own pool, a process
+ * whose device memory is already fully reserved by another framework's
+ * caching allocator, or a latency-critical loop that cannot afford the
+ * implicit device synchronisation of an allocation.  It needs no handle and
+ * allocates nothing: the caller passes the inputs and outputs exactly as for
+ * wsm_iterate (same meaning, layout and results), and the kernel's scratch
+ * (sorted center tables, cluster sums, SSE partials and trace, barrier
+ * words) lives in one file-scope device array of about 1.13 MiB that every
+ * GPU which loads libwsm keeps until the process exits.
+ *   - Limits: 1 <= K <= 256, 1 <= n_unique <= 2^24, 0 <= max_iter <= 4096;
+ *     larger sizes are rejected with WSM_E_INVAL and a message.
+ *   - The first call on each device looks up the array's device address and
+ *     the kernel's co-resident grid for that device (with that device
+ *     current); make that first call before any stream capture begins.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind; each call clears the words that must start at zero.  Calls
+ *     whose executions overlap on the GPU (other streams, other host
+ *     threads) race on the array and give wrong results: order them.
+ *   - iters_done / sse_trace as for wsm_iterate (if either is given the call
+ *     synchronises and reports device-side failures). */
+WSM_API int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_counts,
+                                int64_t n_unique, int K, float* d_centers, uint8_t* d_labels,
+                                int max_iter, double eps, int* iters_done, double* sse_trace,
+                                wsm_stream stream);
+
 /* Sec. 1, pixel mapping.  One more pruned assignment of the unique colors
  * against d_centers (starting from d_labels, which it updates), a scatter
  * of the memberships into the handle's 2^24-entry color->label table, and

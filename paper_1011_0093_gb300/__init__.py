@@ -8,9 +8,10 @@ points, ``quantize`` chains them for one image.  PyTorch only provides device
 memory and streams.
 """
 from ._native import (MAX_K, MAX_PIXELS, Handle, WsmError, lib, wsm_distortion, wsm_init,
-                      wsm_iterate, wsm_iterate_stats, wsm_map, wsm_reduce, wsm_sync_status)
+                      wsm_iterate, wsm_iterate_noalloc, wsm_iterate_stats, wsm_map, wsm_reduce,
+                      wsm_sync_status)
 from .quantize import Quantized, quantize
 
 __all__ = ["MAX_K", "MAX_PIXELS", "Handle", "WsmError", "lib", "wsm_reduce", "wsm_init",
-           "wsm_iterate", "wsm_iterate_stats", "wsm_map", "wsm_distortion", "wsm_sync_status",
+           "wsm_iterate", "wsm_iterate_noalloc", "wsm_iterate_stats", "wsm_map", "wsm_distortion", "wsm_sync_status",
            "Quantized", "quantize"]

@@ -38,6 +38,8 @@ SIGNATURES = {
     "wsm_iterate": (C.c_int, [_P, _P, _P, _I64, C.c_int, _P, _P, C.c_int, C.c_double,
                               C.POINTER(C.c_int), _P, _P]),
     "wsm_iterate_stats": (C.c_int, [_P, C.c_int, C.POINTER(_I64), _P, _P, _P]),
+    "wsm_iterate_noalloc": (C.c_int, [_P, _P, _I64, C.c_int, _P, _P, C.c_int, C.c_double,
+                                      C.POINTER(C.c_int), _P, _P]),
     "wsm_map": (C.c_int, [_P, _P, _I64, C.c_int, _P, _I64, _P, C.c_int, _P, _P, _P]),
     "wsm_distortion": (C.c_int, [_P, _P, _I64, C.c_int, _P, C.c_int, _P, _P,
                                  C.POINTER(C.c_double), _P]),
@@ -167,6 +169,26 @@ def wsm_iterate(h: Handle, colors: torch.Tensor, counts: torch.Tensor, n_unique:
                              _dev(labels, torch.uint8, "labels", n_unique), max_iter, float(eps),
                              C.byref(it) if sync else None,
                              C.cast(trace, C.c_void_p) if sync else None, _stream(stream)))
+    if not sync:
+        return None
+    return it.value, [trace[i] for i in range(min(it.value, max_iter))]
+
+
+def wsm_iterate_noalloc(colors: torch.Tensor, counts: torch.Tensor, n_unique: int, K: int,
+                        centers: torch.Tensor, labels: torch.Tensor, max_iter: int, eps: float,
+                        sync: bool = True, stream=None):
+    """wsm_iterate without a handle and without any device allocation, for
+    callers that cannot allocate (see include/wsm.h).  Same arguments and
+    results as wsm_iterate; calls that overlap on the GPU race."""
+    it = C.c_int(0)
+    trace = (C.c_double * max(max_iter, 1))()
+    _check(lib().wsm_iterate_noalloc(_dev(colors, torch.uint32, "colors", n_unique),
+                                     _dev(counts, torch.uint32, "counts", n_unique), n_unique, K,
+                                     _dev(centers, torch.float32, "centers", 4 * K),
+                                     _dev(labels, torch.uint8, "labels", n_unique), max_iter,
+                                     float(eps), C.byref(it) if sync else None,
+                                     C.cast(trace, C.c_void_p) if sync else None,
+                                     _stream(stream)))
     if not sync:
         return None
     return it.value, [trace[i] for i in range(min(it.value, max_iter))]

@@ -22,6 +22,7 @@
 // the same 16-byte load.  The center index of an entry is only read when a
 // visited center becomes the new minimum.
 #include <algorithm>
+#include <mutex>
 
 #include "wsm_internal.cuh"
 
@@ -359,6 +360,131 @@ extern "C" int wsm_iterate_stats(wsm_handle* h, int K, int64_t* evaluated, int64
             if (S)
                 for (int ch = 0; ch < 3; ++ch) S[3 * k + ch] = (int64_t)buf[4 * k + ch];
             if (W) W[k] = (int64_t)buf[4 * k + 3];
+        }
+    }
+    return WSM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// wsm_iterate_noalloc: the same Sort-Means iterations for callers that may
+// not allocate device memory (see include/wsm.h).  All scratch lives in the
+// file-scope array below, which every GPU that loads this library holds
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace wsm {
+
+constexpr int kStaticMaxK = WSM_MAX_K;
+constexpr int kStaticMaxGrid = 1024;
+constexpr size_t kStaticTabBytes = sizeof(float4) * kStaticMaxK * kStaticMaxK;   // 1 MiB
+constexpr size_t kStaticNbBytes = (size_t)kStaticMaxK * kStaticMaxK;            // 64 KiB
+constexpr size_t kStaticAccBytes = sizeof(unsigned long long) * 2 * 4 * kStaticMaxK;
+constexpr size_t kStaticSseBytes = sizeof(double) * 2 * kStaticMaxGrid;
+constexpr size_t kStaticTraceBytes = sizeof(double) * kMaxTrace;
+constexpr size_t kStaticOffNb = kStaticTabBytes;
+constexpr size_t kStaticOffAcc = kStaticOffNb + kStaticNbBytes;
+constexpr size_t kStaticOffSse = kStaticOffAcc + kStaticAccBytes;
+constexpr size_t kStaticOffTrace = kStaticOffSse + kStaticSseBytes;
+constexpr size_t kStaticOffCtrl = kStaticOffTrace + kStaticTraceBytes;
+constexpr size_t kStaticBytes = kStaticOffCtrl + 256;           // about 1.13 MiB in total
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+struct StaticSetup {
+    bool ready = false;
+    unsigned char* scratch = nullptr;   // device address of g_static_scratch
+    int grid = 0;
+};
+static std::mutex g_static_mutex;
+static StaticSetup g_static_setup[64];
+
+// Once per device, with that device current: the device address of the
+// scratch array and the co-resident grid of the persistent kernel.
+static int static_setup(int dev, StaticSetup** out) {
+    if (dev < 0 || dev >= 64) return fail(WSM_E_STATE, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    StaticSetup& st = g_static_setup[dev];
+    if (!st.ready) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        int sms = 0, occ = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &occ, k_sortmeans<false>, kIterThreads, sortmeans_smem(kStaticMaxK));
+        if (e != cudaSuccess) return cuda_fail(e, "static set-up query");
+        if (occ < 1) return fail(WSM_E_CUDA, "persistent kernel cannot be resident");
+        st.scratch = static_cast<unsigned char*>(p);
+        st.grid = std::min(std::min(occ, 2) * sms, kStaticMaxGrid);
+        st.ready = true;
+    }
+    *out = &st;
+    return WSM_OK;
+}
+
+}  // namespace wsm
+
+extern "C" int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_counts,
+                                   int64_t n_unique, int K, float* d_centers, uint8_t* d_labels,
+                                   int max_iter, double eps, int* iters_done, double* sse_trace,
+                                   wsm_stream stream) {
+    if (K < 1 || K > kStaticMaxK)
+        return fail(WSM_E_INVAL, "wsm_iterate_noalloc: K must be in [1, 256] (the static "
+                                 "scratch holds 256 x 256 sorted center tables)");
+    if (n_unique < 1 || n_unique > WSM_MAX_PIXELS)
+        return fail(WSM_E_INVAL, "wsm_iterate_noalloc: n_unique must be in [1, 2^24]");
+    if (max_iter < 0 || max_iter > kMaxTrace)
+        return fail(WSM_E_INVAL, "wsm_iterate_noalloc: max_iter must be in [0, 4096]");
+    if (!d_colors || !d_counts || !d_centers || !d_labels)
+        return fail(WSM_E_INVAL, "null device pointer");
+    if ((uintptr_t)d_centers & 15) return fail(WSM_E_INVAL, "centers must be 16-byte aligned");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    StaticSetup* st = nullptr;
+    int rc = static_setup(dev, &st);
+    if (rc != WSM_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* base = st->scratch;
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(base + kStaticOffCtrl);
+    SortMeansParams P;
+    P.colors = d_colors;
+    P.counts = d_counts;
+    P.n = n_unique;
+    P.K = K;
+    P.centers = reinterpret_cast<float4*>(d_centers);
+    P.labels = d_labels;
+    P.max_iter = max_iter;
+    P.eps = eps;
+    P.tab = reinterpret_cast<float4*>(base);
+    P.tab_nb = base + kStaticOffNb;
+    P.acc = reinterpret_cast<unsigned long long*>(base + kStaticOffAcc);
+    P.sse_part = reinterpret_cast<double*>(base + kStaticOffSse);
+    P.trace = reinterpret_cast<double*>(base + kStaticOffTrace);
+    P.lut = nullptr;
+    P.ctrl = ctrl;
+    int64_t want = (n_unique + kIterThreads - 1) / kIterThreads;
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, st->grid));
+    void* args[] = {&P};
+    // the barrier words, counters and status word start at zero on every call
+    e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s);
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel((void*)k_sortmeans<false>, grid, kIterThreads, args,
+                                        sortmeans_smem(K), s);
+    if (e != cudaSuccess) return cuda_fail(e, "wsm_iterate_noalloc launch");
+    if (iters_done || sse_trace) {
+        Ctrl host;
+        e = cudaMemcpyAsync(&host, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "wsm_iterate_noalloc result copy");
+        if (host.status & ST_TIMEOUT) return fail(WSM_E_TIMEOUT, "a device-side grid barrier timed out");
+        if (host.status & ST_BAD_LABEL) return fail(WSM_E_INVAL, "a membership was >= K");
+        if (iters_done) *iters_done = host.iters_done;
+        if (sse_trace && host.iters_done > 0) {
+            e = cudaMemcpyAsync(sse_trace, P.trace, sizeof(double) * std::min(host.iters_done, max_iter),
+                                cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(e, "wsm_iterate_noalloc trace copy");
         }
     }
     return WSM_OK;
