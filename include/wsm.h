@@ -172,7 +172,7 @@ WSM_API int wsm_iterate_stats(wsm_handle* h, int K, int64_t* evaluated, int64_t*
  * allocates nothing: the caller passes the inputs and outputs exactly as for
  * wsm_iterate (same meaning, layout and results), and the kernel's scratch
  * (sorted center tables, cluster sums, SSE partials and trace, barrier
- * words) lives in one file-scope device array of about 1.13 MiB that every
+ * words) lives in one file-scope device array of about 1.2 MiB that every
  * GPU which loads libwsm keeps until the process exits.
  *   - Limits: 1 <= K <= 256, 1 <= n_unique <= 2^24, 0 <= max_iter <= 4096;
  *     larger sizes are rejected with WSM_E_INVAL and a message.
@@ -201,7 +201,9 @@ WSM_API int wsm_map(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, int p
             uint8_t* d_labels, uint8_t* d_index, wsm_stream stream);
 
 /* Sec. 3.1, Eq. 2: MSE = (1/N) sum_p ||x_p - c_{index_p}||^2 over the three
- * channels, accumulated in FP64 in a fixed order (deterministic).
+ * channels.  Each pixel's squared distance (FP32, difference form) is
+ * truncated to units of 2^-20 and summed as an integer, so the result does
+ * not depend on the order of the additions (deterministic).
  *   d_mse  device double (may be NULL); mse host double (may be NULL; if
  *          given, the call synchronises).
  * Errors: WSM_E_INVAL (sizes, K; index >= K found). */

@@ -137,8 +137,9 @@ extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64
         {(void**)&h->lut, (size_t)kHistBins},
         {(void**)&h->tab, sizeof(float4) * kk},
         {(void**)&h->tab_nb, kk},
-        {(void**)&h->acc, sizeof(unsigned long long) * 2 * 4 * max_K},
-        {(void**)&h->sse_part, sizeof(double) * 2 * h->iter_grid},
+        {(void**)&h->sums, sizeof(unsigned) * 2 * kCopies * 4 * (size_t)max_K},
+        {(void**)&h->sums64, sizeof(unsigned long long) * 2 * kCopies * 4},
+        {(void**)&h->acc, sizeof(unsigned long long) * 4 * max_K},
         {(void**)&h->trace, sizeof(double) * kMaxTrace},
         {(void**)&h->mse_part, sizeof(double) * 1032},   // 1024 partials + result
         {(void**)&h->ctrl, sizeof(Ctrl)},
@@ -158,7 +159,7 @@ extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64
     e = cudaMemset(h->hist, 0, sizeof(uint32_t) * kHistBins);
     if (e == cudaSuccess) e = cudaMemset(h->bitmap, 0, sizeof(uint32_t) * kMapWords);
     if (e == cudaSuccess) e = cudaMemset(h->ctrl, 0, sizeof(Ctrl));
-    if (e == cudaSuccess) e = cudaMemset(h->acc, 0, sizeof(unsigned long long) * 8 * max_K);
+    if (e == cudaSuccess) e = cudaMemset(h->acc, 0, sizeof(unsigned long long) * 4 * max_K);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         wsm_destroy(h);
@@ -174,8 +175,8 @@ extern "C" int wsm_destroy(wsm_handle* h) {
     cudaGetDevice(&prev);
     if (h->device >= 0 && prev != h->device) cudaSetDevice(h->device);
     cudaDeviceSynchronize();
-    void* dev_ptrs[] = {h->hist, h->bitmap, h->blk_total, h->lut, h->tab, h->tab_nb,
-                        h->acc, h->sse_part, h->trace, h->mse_part, h->ctrl};
+    void* dev_ptrs[] = {h->hist, h->bitmap, h->blk_total, h->lut, h->tab, h->tab_nb, h->sums,
+                        h->sums64, h->acc, h->trace, h->mse_part, h->ctrl};
     for (void* p : dev_ptrs)
         if (p) cudaFree(p);
     if (h->host_ctrl) cudaFreeHost(h->host_ctrl);

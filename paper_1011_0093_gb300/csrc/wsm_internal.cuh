@@ -24,28 +24,28 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 constexpr int kHistBins = 1 << 24;           // one bin per 24-bit color
 constexpr int kMapWords = kHistBins / 32;    // occupancy bitmap words
-constexpr int kScanWordsPerThread = 8;       // bitmap words per thread in the compaction
-constexpr int kScanThreads = 256;
+constexpr int kScanWordsPerThread = 4;       // bitmap words per thread in the compaction
+constexpr int kScanThreads = 512;
 constexpr int kScanWordsPerBlock = kScanWordsPerThread * kScanThreads;   // 2048
 constexpr int kScanBlocks = kMapWords / kScanWordsPerBlock;             // 256
 constexpr int kIterThreads = 512;            // threads per block of the persistent kernel
 constexpr int kMaxTrace = 4096;              // SSE values kept per wsm_iterate call
+constexpr int kCopies = 8;                   // replicas of the global accumulators
+constexpr int kChunk = 32;                   // colors per warp chunk (one per lane)
 
 // Control words in device memory (one block per handle).
-// The first kLaunchResetBytes bytes are cleared before every persistent
-// launch, so a barrier abandoned after a timeout cannot confuse the next one.
+// The fields before `status` are cleared before every persistent launch, so
+// a barrier abandoned after a timeout cannot confuse the next launch.
 struct Ctrl {
-    unsigned bar_count;        // grid barrier: arrivals
-    unsigned bar_gen;          // grid barrier: generation
+    unsigned bar_count;        // grid barrier: monotonic arrival counter
     int iters_done;            // iterations completed by the last wsm_iterate
-    unsigned reserved;
     unsigned long long evaluated;  // distances computed by the last persistent launch
     unsigned status;           // ST_* bits (cleared only when read by the host)
-    unsigned reserved2;
+    unsigned reserved;
     int64_t n_unique;          // N' of the last wsm_reduce
     double mse;                // host mirror slot of the last wsm_distortion
 };
-constexpr size_t kLaunchResetBytes = 24;
+constexpr size_t kLaunchResetBytes = 16;
 static_assert(offsetof(Ctrl, status) == kLaunchResetBytes, "Ctrl layout");
 
 }  // namespace wsm
@@ -65,8 +65,9 @@ struct wsm_handle {
     uint8_t* lut = nullptr;      // [2^24] color -> label
     float4* tab = nullptr;       // [max_K * max_K] sorted rows: (d/4, c.x, c.y, c.z)
     uint8_t* tab_nb = nullptr;   // [max_K * max_K] center index of each row entry
-    unsigned long long* acc = nullptr;  // [2][max_K][4]: S_k (3) and W_k
-    double* sse_part = nullptr;  // [2][iter_grid]
+    unsigned* sums = nullptr;    // [2][kCopies][4 max_K] replicated cluster sums
+    unsigned long long* sums64 = nullptr;  // [2][kCopies][4] SSE, distances, pixels, nonzero
+    unsigned long long* acc = nullptr;  // [max_K][4]: S_k (3) and W_k of the last pass
     double* trace = nullptr;     // [kMaxTrace]
     double* mse_part = nullptr;  // [1024] block partials + [1] result
     wsm::Ctrl* ctrl = nullptr;
@@ -96,44 +97,49 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
-// Grid-wide barrier for a cooperative launch of `nblocks` co-resident
-// blocks.  Thread 0 of each block arrives on a counter; the last arrival
-// resets it and advances the generation word; the others spin on the
-// generation with a time limit.  On a timeout the status word gets
-// ST_TIMEOUT and the function returns false in every thread of the block
-// (also when another block recorded a failure).  Memory written before the
-// barrier by any block is visible to every block after it.
+__device__ __forceinline__ unsigned add_release(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;"
+                 : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Grid-wide barrier for a cooperative launch of `nblocks` co-resident blocks.
+// Thread 0 of each block adds 1 to a counter that only grows (release), and
+// waits (acquire) until it reaches the next multiple of nblocks, i.e. until
+// every block has arrived at this barrier.  The wait has a time limit: past
+// it the status word gets ST_TIMEOUT and the function returns false in every
+// thread of the block.  Memory written before the barrier by any block is
+// visible to every block after it.
 __device__ __forceinline__ bool grid_sync(Ctrl* ctrl, unsigned nblocks) {
     __shared__ unsigned s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned gen = ld_acquire(&ctrl->bar_gen);
-        __threadfence();
-        unsigned arrived = atomicAdd(&ctrl->bar_count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&ctrl->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctrl->bar_gen, 1u);
-        } else {
+        unsigned old = add_release(&ctrl->bar_count, 1u);
+        unsigned target = (old / nblocks + 1u) * nblocks;
+        unsigned ok = 1u;
+        if ((int)(ld_acquire(&ctrl->bar_count) - target) < 0) {
             unsigned long long t0 = global_ns();
-            while (ld_acquire(&ctrl->bar_gen) == gen) {
+            while ((int)(ld_acquire(&ctrl->bar_count) - target) < 0) {
                 if (global_ns() - t0 > kWaitLimitNs) {
                     atomicOr(&ctrl->status, ST_TIMEOUT);
+                    ok = 0u;
                     break;
                 }
-                __nanosleep(40);
             }
         }
-        __threadfence();
-        s_ok = (ld_acquire(&ctrl->status) & ST_TIMEOUT) ? 0u : 1u;
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
 }
 
+// Squared distance in the difference form with one fixed rounding order
+// (no contraction choices left to the compiler), so that every call site --
+// center table, previous-center distance, visited entries -- rounds alike.
 __device__ __forceinline__ float sq3(float ax, float ay, float az, float bx, float by, float bz) {
-    float ex = ax - bx, ey = ay - by, ez = az - bz;
-    return ex * ex + ey * ey + ez * ez;
+    const float ex = __fsub_rn(ax, bx), ey = __fsub_rn(ay, by), ez = __fsub_rn(az, bz);
+    return __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
 }
 
 }  // namespace wsm

@@ -36,48 +36,63 @@ __global__ void __launch_bounds__(256) k_gather(const uint8_t* __restrict__ rgb,
 constexpr int kMseThreads = 256;
 constexpr int kMseMaxBlocks = 1024;
 
-// Per-block FP64 partial sums of ||x_p - c_{index_p}||^2, each block over a
-// fixed contiguous range, reduced in a fixed order (deterministic).
+// v * 2^20 truncated toward zero, for v >= 0 finite below 2^18, from the FP32
+// bits of v (exact integer arithmetic).
+__device__ __forceinline__ unsigned long long to_fixed20(float v) {
+    const unsigned bits = __float_as_uint(v);
+    int e = (bits >> 23) & 255;
+    unsigned long long m = bits & 0x7FFFFFu;
+    if (e) m |= 0x800000u;
+    else e = 1;
+    const int sh = e - 150 + 20;                // v = m * 2^(e-150)
+    if (sh >= 0) return m << min(sh, 40);
+    if (sh <= -63) return 0ull;
+    return m >> (-sh);
+}
+
+// Per-block sums of ||x_p - c_{index_p}||^2, each pixel's FP32 squared
+// distance truncated to units of 2^-20 and added as an integer, so the total
+// does not depend on the order of the additions.
 __global__ void __launch_bounds__(kMseThreads) k_mse_partial(
     const uint8_t* __restrict__ rgb, int64_t n, int stride, const float4* __restrict__ centers,
-    int K, const uint8_t* __restrict__ index, double* __restrict__ part, Ctrl* ctrl) {
+    int K, const uint8_t* __restrict__ index, unsigned long long* __restrict__ part, Ctrl* ctrl) {
     __shared__ float4 s_c[WSM_MAX_K];
-    __shared__ double s_red[kMseThreads / 32];
+    __shared__ unsigned long long s_red[kMseThreads / 32];
     for (int k = threadIdx.x; k < K; k += blockDim.x) s_c[k] = centers[k];
     __syncthreads();
-    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t begin = (int64_t)blockIdx.x * chunk;
-    const int64_t end = min(n, begin + chunk);
-    double acc = 0.0;
+    unsigned long long acc = 0;
     bool bad = false;
-    for (int64_t p = begin + threadIdx.x; p < end; p += blockDim.x) {
-        int k = index[p];
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int k = index[p];
         if (k >= K) {
             bad = true;
             continue;
         }
-        uint32_t key = key_of(rgb, p, stride);
-        float4 c = s_c[k];
-        acc += (double)sq3((float)((key >> 16) & 255u), (float)((key >> 8) & 255u),
-                           (float)(key & 255u), c.x, c.y, c.z);
+        const uint32_t key = key_of(rgb, p, stride);
+        const float4 c = s_c[k];
+        acc += to_fixed20(sq3((float)((key >> 16) & 255u), (float)((key >> 8) & 255u),
+                              (float)(key & 255u), c.x, c.y, c.z));
     }
     if (bad) atomicOr(&ctrl->status, ST_BAD_LABEL);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
+        unsigned long long t = 0;
         for (int w = 0; w < kMseThreads / 32; ++w) t += s_red[w];
         part[blockIdx.x] = t;
     }
 }
 
-__global__ void k_mse_final(const double* __restrict__ part, int nparts, int64_t n,
+// One warp adds the block sums and writes MSE = total * 2^-20 / N.
+__global__ void k_mse_final(const unsigned long long* __restrict__ part, int nparts, int64_t n,
                             double* __restrict__ out, double* __restrict__ out2) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < nparts; ++i) t += part[i];
-        double m = n > 0 ? t / (double)n : 0.0;
+    unsigned long long t = 0;
+    for (int i = threadIdx.x; i < nparts; i += 32) t += part[i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+    if (threadIdx.x == 0) {
+        const double m = n > 0 ? (double)t * (1.0 / 1048576.0) / (double)n : 0.0;
         *out = m;
         if (out2) *out2 = m;
     }
@@ -132,11 +147,12 @@ extern "C" int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pix
         return fail(WSM_E_INVAL, "4-byte pixels must be 4-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     int64_t want = (n_pixels + 4 * kMseThreads - 1) / (4 * kMseThreads);
-    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, kMseMaxBlocks));
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min(kMseMaxBlocks, 4 * h->sms)));
+    unsigned long long* part = reinterpret_cast<unsigned long long*>(h->mse_part);
     k_mse_partial<<<grid, kMseThreads, 0, s>>>(d_rgb, n_pixels, pixel_stride,
                                                 reinterpret_cast<const float4*>(d_centers), K,
-                                                d_index, h->mse_part, h->ctrl);
-    k_mse_final<<<1, 32, 0, s>>>(h->mse_part, grid, n_pixels, h->mse_part + kMseMaxBlocks, d_mse);
+                                                d_index, part, h->ctrl);
+    k_mse_final<<<1, 32, 0, s>>>(part, grid, n_pixels, h->mse_part + kMseMaxBlocks, d_mse);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "distortion launch");
     if (mse) {

@@ -48,11 +48,9 @@ __global__ void __launch_bounds__(256) k_hist24(const uint8_t* __restrict__ rgb,
 // Pass 1 of the compaction: the number of set bits in each block's 2048 words.
 __global__ void __launch_bounds__(kScanThreads) k_scan_count(const uint32_t* __restrict__ bitmap,
                                                              uint32_t* __restrict__ blk_total) {
-    const uint4* w = reinterpret_cast<const uint4*>(bitmap) +
-                     ((size_t)blockIdx.x * kScanWordsPerBlock + threadIdx.x * kScanWordsPerThread) / 4;
-    uint4 a = w[0], b = w[1];
-    unsigned c = __popc(a.x) + __popc(a.y) + __popc(a.z) + __popc(a.w) + __popc(b.x) +
-                 __popc(b.y) + __popc(b.z) + __popc(b.w);
+    const uint4 a = reinterpret_cast<const uint4*>(bitmap)[
+        ((size_t)blockIdx.x * kScanWordsPerBlock + threadIdx.x * kScanWordsPerThread) / 4];
+    unsigned c = __popc(a.x) + __popc(a.y) + __popc(a.z) + __popc(a.w);
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
     __shared__ unsigned s_w[kScanThreads / 32];
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
@@ -65,13 +63,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_count(const uint32_t* __r
 }
 
 // Pass 2: each block finds its output offset from the totals of the blocks
-// before it, scans its threads' bit counts, and emits (color, count) for every
-// set bit in ascending order, zeroing the bins and words it consumed.
+// before it, scans its words' bit counts into per-word output offsets, and
+// then emits (color, count) for every set bit: a warp takes one word at a
+// time, lane l handles bit l (so the 32 bins of a word are read and cleared
+// with one coalesced access), kEmitBatch words in flight per warp.  Output
+// order is ascending color order.
 __global__ void __launch_bounds__(kScanThreads) k_scan_emit(
     uint32_t* __restrict__ bitmap, uint32_t* __restrict__ hist,
     const uint32_t* __restrict__ blk_total, uint32_t* __restrict__ colors,
     uint32_t* __restrict__ counts, int64_t capacity, int64_t* __restrict__ d_n_unique,
     Ctrl* __restrict__ ctrl) {
+    __shared__ uint32_t s_word[kScanWordsPerBlock];
+    __shared__ uint32_t s_off[kScanWordsPerBlock];
     __shared__ unsigned s_w[kScanThreads / 32];
     __shared__ unsigned long long s_base;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -82,44 +85,60 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_emit(
     if (tid == 0) s_base = 0;
     __syncthreads();
     if (lane == 0 && before) atomicAdd(&s_base, before);
-    const size_t w0 = (size_t)blockIdx.x * kScanWordsPerBlock + (size_t)tid * kScanWordsPerThread;
-    uint4* wv = reinterpret_cast<uint4*>(bitmap) + w0 / 4;
-    uint4 a = wv[0], b = wv[1];
-    uint32_t words[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    const size_t w0 = (size_t)blockIdx.x * kScanWordsPerBlock;
+    uint4* wv = reinterpret_cast<uint4*>(bitmap + w0) + tid;
+    const uint4 a = wv[0];
+    const uint32_t words[4] = {a.x, a.y, a.z, a.w};
     unsigned mine = 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) mine += __popc(words[i]);
+    for (int i = 0; i < 4; ++i) mine += __popc(words[i]);
     // block-wide exclusive scan of `mine`
     unsigned incl = mine;
     for (int o = 1; o < 32; o <<= 1) {
-        unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
         if (lane >= o) incl += v;
     }
     if (lane == 31) s_w[wid] = incl;
     __syncthreads();
     unsigned warp_off = 0;
     for (int i = 0; i < wid; ++i) warp_off += s_w[i];
-    int64_t pos = (int64_t)s_base + warp_off + (incl - mine);
+    unsigned off = warp_off + (incl - mine);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        uint32_t m = words[i];
-        while (m) {
-            int bit = __ffs(m) - 1;
-            m &= m - 1;
-            uint32_t key = (uint32_t)((w0 + i) << 5) | (uint32_t)bit;
-            uint32_t cnt = hist[key];
-            hist[key] = 0;
-            if (pos < capacity) {
-                colors[pos] = key;
-                counts[pos] = cnt;
-            }
-            ++pos;
-        }
+    for (int i = 0; i < 4; ++i) {
+        s_word[4 * tid + i] = words[i];
+        s_off[4 * tid + i] = off;
+        off += __popc(words[i]);
     }
     if (a.x | a.y | a.z | a.w) wv[0] = make_uint4(0, 0, 0, 0);
-    if (b.x | b.y | b.z | b.w) wv[1] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    const int64_t base = (int64_t)s_base;
+    const unsigned below = (1u << lane) - 1u;
+    constexpr int kWordsPerWarp = kScanWordsPerBlock / (kScanThreads / 32);
+    constexpr int kEmitBatch = 16;
+    static_assert(kWordsPerWarp % kEmitBatch == 0, "emit batches");
+    for (int q = wid * kWordsPerWarp; q < (wid + 1) * kWordsPerWarp; q += kEmitBatch) {
+        uint32_t wd[kEmitBatch], cnt[kEmitBatch];
+#pragma unroll
+        for (int u = 0; u < kEmitBatch; ++u) {
+            wd[u] = s_word[q + u];
+            cnt[u] = 0;
+            if ((wd[u] >> lane) & 1u) cnt[u] = hist[((w0 + q + u) << 5) | lane];
+        }
+#pragma unroll
+        for (int u = 0; u < kEmitBatch; ++u) {
+            if ((wd[u] >> lane) & 1u) {
+                const uint32_t key = (uint32_t)((w0 + q + u) << 5) | (uint32_t)lane;
+                const int64_t pos = base + s_off[q + u] + __popc(wd[u] & below);
+                hist[key] = 0;
+                if (pos < capacity) {
+                    colors[pos] = key;
+                    counts[pos] = cnt[u];
+                }
+            }
+        }
+    }
     if (blockIdx.x == gridDim.x - 1 && tid == kScanThreads - 1) {
-        int64_t total = pos;   // last thread of the last block ends at N'
+        const int64_t total = base + off;   // the last thread of the last block ends at N'
         ctrl->n_unique = total;
         if (d_n_unique) *d_n_unique = total;
         if (total > capacity) atomicOr(&ctrl->status, ST_CAPACITY);
