@@ -137,7 +137,7 @@ extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64
         {(void**)&h->lut, (size_t)kHistBins},
         {(void**)&h->tab, sizeof(float4) * kk},
         {(void**)&h->tab_nb, kk},
-        {(void**)&h->sums, sizeof(unsigned) * 2 * kCopies * 4 * (size_t)max_K},
+        {(void**)&h->sums, sizeof(unsigned) * 2 * kCopies * 5 * (size_t)max_K},
         {(void**)&h->sums64, sizeof(unsigned long long) * 2 * kCopies * 4},
         {(void**)&h->acc, sizeof(unsigned long long) * 4 * max_K},
         {(void**)&h->trace, sizeof(double) * kMaxTrace},

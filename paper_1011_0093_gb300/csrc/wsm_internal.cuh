@@ -65,7 +65,7 @@ struct wsm_handle {
     uint8_t* lut = nullptr;      // [2^24] color -> label
     float4* tab = nullptr;       // [max_K * max_K] sorted rows: (d/4, c.x, c.y, c.z)
     uint8_t* tab_nb = nullptr;   // [max_K * max_K] center index of each row entry
-    unsigned* sums = nullptr;    // [2][kCopies][4 max_K] replicated cluster sums
+    unsigned* sums = nullptr;    // [2][kCopies][5 max_K] replicated cluster sums and maxima
     unsigned long long* sums64 = nullptr;  // [2][kCopies][4] SSE, distances, pixels, nonzero
     unsigned long long* acc = nullptr;  // [max_K][4]: S_k (3) and W_k of the last pass
     double* trace = nullptr;     // [kMaxTrace]

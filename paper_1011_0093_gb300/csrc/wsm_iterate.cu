@@ -8,8 +8,12 @@
 //      keeps its center), measures that pass's SSE and applies the Sec. 3.2
 //      stop rule (all blocks compute the same values, so all decide alike),
 //      then sorts rows p = b, b+G, ... of the center table: row p lists,
-//      nearest first, the entries (d[p][t] / 4, c_t) for all centers t, ties
-//      ordered by (t != p, t), so entry 0 is p itself.
+//      nearest first, the entries (d[p][t] / 4, c_t) for the centers t, ties
+//      ordered by (t != p, t), so entry 0 is p itself.  In the first pass of
+//      a launch a row holds every center; later a row holds only the centers
+//      below a bound that no visit of that row can pass (see the row bound
+//      below), followed by entries with an infinite bound -- the entries a
+//      visit reads, and their order, are the same as with the full row.
 //   B  the pruned nearest-center search, one lane per unique color; warp w
 //      of block b takes the chunks of 32 consecutive colors numbered
 //      b * WPB + w + k * G * WPB (spreading costly regions of color space over
@@ -47,7 +51,9 @@ struct SortMeansParams {
     double eps;
     float4* tab;           // [K*K] rows of (d/4, c.x, c.y, c.z), nearest first
     uint8_t* tab_nb;       // [K*K] center index of each entry
-    unsigned* sums;        // [2][kCopies][4K] cluster sums, double-buffered by pass parity
+    unsigned* sums;        // [2][kCopies][5K] cluster sums (4K) and the largest squared
+                           //   distance of a member to its center (K, FP32 bits),
+                           //   double-buffered by pass parity
     unsigned long long* sums64;  // [2][kCopies][4] SSE (2^-20 units), distances, pixels,
                                  //   colors with a nonzero minimum
     unsigned long long* acc;     // [K][4] cluster sums of the last pass
@@ -119,28 +125,53 @@ __device__ __forceinline__ unsigned long long row_key(float d, int t, int p) {
     return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(t == p ? 0 : t + 1);
 }
 
-// This block's rows of the sorted center table.  For K > 128 every warp of
-// the block sorts its own rows (sort_row_warp); otherwise the rank of every
-// key of
-// row p among the row's keys (keys are distinct) is its entry position; S
-// threads share one key's comparisons and add their partial ranks.
+// This block's rows of the sorted center table.  Row p keeps the centers t
+// with d[p][t] < thr[p] (p itself always), sorted by rank: the rank of a key
+// among the kept keys (keys are distinct) is its entry position, S threads
+// share one key's comparisons.  Four entries with an infinite bound follow
+// the kept ones, so every visit stops there (the scan reads four entries per
+// step).  thr = NULL keeps every center.
 __device__ __forceinline__ void build_rows(const SortMeansParams& P, const float4* s_c,
-                                           unsigned long long* s_key, int* s_rank) {
-    const int K = P.K, tid = threadIdx.x, T = blockDim.x;
-    const int S = max(1, T / K);
-    const int span = (K + S - 1) / S;
+                                           const float* thr, unsigned long long* s_key,
+                                           int* s_rank, int* s_cnt) {
+    const int K = P.K, tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
     for (int p = blockIdx.x; p < K; p += gridDim.x) {
         const float4 cp = s_c[p];
-        for (int t = tid; t < K; t += T) {
-            const float4 ct = s_c[t];
-            s_key[t] = row_key(sq3(cp.x, cp.y, cp.z, ct.x, ct.y, ct.z), t, p);
-            s_rank[t] = 0;
+        const float bound = thr ? thr[p] : __int_as_float(0x7f800000);
+        // kept centers, compacted in index order (K <= 256 <= T: one round)
+        {
+            const int t = tid;
+            float d = 0.f;
+            bool keep = false;
+            if (t < K) {
+                const float4 ct = s_c[t];
+                d = sq3(cp.x, cp.y, cp.z, ct.x, ct.y, ct.z);
+                keep = d < bound || t == p;
+            }
+            const unsigned vote = __ballot_sync(0xFFFFFFFFu, keep);
+            if (lane == 0) s_cnt[wid] = __popc(vote);
+            __syncthreads();
+            if (tid == 0) {
+                int run = 0;
+                for (int w = 0; w < (T >> 5); ++w) {
+                    const int c = s_cnt[w];
+                    s_cnt[w] = run;
+                    run += c;
+                }
+                s_cnt[32] = run;
+            }
+            __syncthreads();
+            if (keep) s_key[s_cnt[wid] + __popc(vote & ((1u << lane) - 1u))] = row_key(d, t, p);
+            if (tid < K) s_rank[tid] = 0;
+            __syncthreads();
         }
-        __syncthreads();
-        for (int t = tid; t < S * K; t += T) {
-            const int j = t % K, h = t / K;
+        const int L = s_cnt[32];
+        const int S = max(1, T / L);
+        const int span = (L + S - 1) / S;
+        for (int t = tid; t < S * L; t += T) {
+            const int j = t % L, h = t / L;
             const unsigned long long kj = s_key[j];
-            const int lo = h * span, hi = min(K, lo + span);
+            const int lo = h * span, hi = min(L, lo + span);
             int rank = 0;
 #pragma unroll 8
             for (int k = lo; k < hi; ++k) rank += s_key[k] < kj;
@@ -148,13 +179,18 @@ __device__ __forceinline__ void build_rows(const SortMeansParams& P, const float
             else if (rank) atomicAdd(s_rank + j, rank);
         }
         __syncthreads();
-        for (int t = tid; t < K; t += T) {
-            const float4 ct = s_c[t];
+        for (int t = tid; t < L; t += T) {
+            const unsigned long long key = s_key[t];
+            const unsigned lo = (unsigned)key;
+            const int c = lo ? (int)lo - 1 : p;
+            const float4 ct = s_c[c];
             const int r = s_rank[t];
             P.tab[(size_t)p * K + r] =
-                make_float4(__uint_as_float((unsigned)(s_key[t] >> 32)) * 0.25f, ct.x, ct.y, ct.z);
-            P.tab_nb[(size_t)p * K + r] = (uint8_t)t;
+                make_float4(__uint_as_float((unsigned)(key >> 32)) * 0.25f, ct.x, ct.y, ct.z);
+            P.tab_nb[(size_t)p * K + r] = (uint8_t)c;
         }
+        if (tid < 4 && L + tid < K)
+            P.tab[(size_t)p * K + L + tid] = make_float4(__int_as_float(0x7f800000), 0.f, 0.f, 0.f);
         __syncthreads();
     }
 }
@@ -173,11 +209,14 @@ template <bool kMap>
 __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P) {
     extern __shared__ float4 smem[];
     const int K = P.K;
-    float4* s_c = smem;                                                       // [K]
-    unsigned* s_acc = reinterpret_cast<unsigned*>(s_c + K);                   // [4K]
-    unsigned long long* s_key = reinterpret_cast<unsigned long long*>(s_acc + 4 * K);  // [K]
-    int* s_rank = reinterpret_cast<int*>(s_key + K);                          // [K]
+    float4* s_c = smem;                                                       // [K] centers
+    float4* s_cn = s_c + K;                                                   // [K] new centers
+    unsigned long long* s_key = reinterpret_cast<unsigned long long*>(s_cn + K);  // [K]
+    unsigned* s_acc = reinterpret_cast<unsigned*>(s_key + K);                 // [5K] sums, max
+    float* s_thr = reinterpret_cast<float*>(s_acc + 5 * K);                   // [K] row bounds
+    int* s_rank = reinterpret_cast<int*>(s_thr + K);                          // [K]
     __shared__ unsigned long long s_red[4][kIterThreads / 32];
+    __shared__ int s_cnt[33];
     __shared__ int s_stop;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -189,11 +228,11 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
 
     for (int k = tid; k < K; k += T) s_c[k] = P.centers[k];
     if (!kMap && b == 0) {
-        for (int j = tid; j < kCopies * 4 * K; j += T) P.sums[j] = 0u;
+        for (int j = tid; j < kCopies * 5 * K; j += T) P.sums[j] = 0u;
         if (tid < 4 * kCopies) P.sums64[tid] = 0ull;
     }
     __syncthreads();
-    build_rows(P, s_c, s_key, s_rank);
+    build_rows(P, s_c, nullptr, s_key, s_rank, s_cnt);
     if (!grid_sync(P.ctrl, G)) return;
 
     unsigned long long prev_fx = 0;        // SSE of the previous pass, in thread 0 only
@@ -201,7 +240,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
         // ---------------- phase B: assignment ----------------
         const int buf = it & 1;
         if (!kMap)
-            for (int j = tid; j < 4 * K; j += T) s_acc[j] = 0u;
+            for (int j = tid; j < 5 * K; j += T) s_acc[j] = 0u;
         __syncthreads();
         unsigned long long sse_fx = 0, ev = 0, npix = 0, nonzero = 0;
         bool bad = false;
@@ -295,6 +334,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
                     atomicAdd(s_acc + 4 * lab + 1, cnt * ((col >> 8) & 255u));
                     atomicAdd(s_acc + 4 * lab + 2, cnt * (col & 255u));
                     atomicAdd(s_acc + 4 * lab + 3, cnt);
+                    atomicMax(s_acc + 4 * K + lab, __float_as_uint(mn));
                     sse_fx += sse_fixed(cnt, mn);
                     npix += cnt;
                     nonzero += mn > 0.f;
@@ -324,24 +364,32 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
         }
         if (kMap) break;
         {
-            unsigned* dst = P.sums + (size_t)(buf * kCopies + copy) * 4 * K;
-            for (int j = tid; j < 4 * K; j += T) {
+            unsigned* dst = P.sums + (size_t)(buf * kCopies + copy) * 5 * K;
+            for (int j = tid; j < 5 * K; j += T) {
                 const unsigned v = s_acc[j];
-                if (v) atomicAdd(dst + j, v);
+                if (v) {
+                    if (j < 4 * K) atomicAdd(dst + j, v);
+                    else atomicMax(dst + j, v);
+                }
             }
         }
         if (!grid_sync(P.ctrl, G)) return;
 
         // ---------------- phase A: totals, centers, stop rule, next table ----------------
         {
-            const unsigned* src = P.sums + (size_t)buf * kCopies * 4 * K;
-            for (int j = tid; j < 4 * K; j += T) {
+            const unsigned* src = P.sums + (size_t)buf * kCopies * 5 * K;
+            for (int j = tid; j < 5 * K; j += T) {
                 unsigned v[kCopies];
 #pragma unroll
-                for (int c = 0; c < kCopies; ++c) v[c] = src[(size_t)c * 4 * K + j];
+                for (int c = 0; c < kCopies; ++c) v[c] = src[(size_t)c * 5 * K + j];
                 unsigned t = 0;
+                if (j < 4 * K) {
 #pragma unroll
-                for (int c = 0; c < kCopies; ++c) t += v[c];
+                    for (int c = 0; c < kCopies; ++c) t += v[c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < kCopies; ++c) t = max(t, v[c]);
+                }
                 s_acc[j] = t;
             }
         }
@@ -379,24 +427,39 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
             }
         }
         if (b == 0) {   // clear the accumulators of the next pass (read last two barriers ago)
-            unsigned* nxt = P.sums + (size_t)(buf ^ 1) * kCopies * 4 * K;
-            for (int j = tid; j < kCopies * 4 * K; j += T) nxt[j] = 0u;
+            unsigned* nxt = P.sums + (size_t)(buf ^ 1) * kCopies * 5 * K;
+            for (int j = tid; j < kCopies * 5 * K; j += T) nxt[j] = 0u;
             if (tid < 4 * kCopies) P.sums64[(size_t)(buf ^ 1) * kCopies * 4 + tid] = 0ull;
         }
         __syncthreads();
         {
-            float* s_cf = reinterpret_cast<float*>(s_c);
+            const float* s_cf = reinterpret_cast<const float*>(s_c);
+            float* s_cnf = reinterpret_cast<float*>(s_cn);
             for (int u = tid; u < 3 * K; u += T) {
                 const int k = u / 3, ch = u - 3 * k;
                 const unsigned w = s_acc[4 * k + 3];
-                if (w) s_cf[4 * k + ch] = div_rn_u32(s_acc[4 * k + ch], w, __frcp_rn((float)w));
+                s_cnf[4 * k + ch] = w ? div_rn_u32(s_acc[4 * k + ch], w, __frcp_rn((float)w))
+                                      : s_cf[4 * k + ch];
             }
             if (b == 0)
                 for (int j = tid; j < 4 * K; j += T) P.acc[j] = s_acc[j];
         }
         __syncthreads();
+        // Row bound for the next pass: a member x of cluster k had
+        // ||x - c_k|| <= sqrt(max_k) against the old center, so against the new
+        // one prev <= (sqrt(max_k) + ||c_k,new - c_k,old||)^2 (triangle
+        // inequality); a visit of row k never goes past 4 prev.  The margin
+        // (x 1.001, + 1e-3) covers the FP32 rounding of these bounds.
+        for (int k = tid; k < K; k += T) {
+            const float4 o = s_c[k], c = s_cn[k];
+            const float r = sqrtf(__uint_as_float(s_acc[4 * K + k])) +
+                            sqrtf(sq3(o.x, o.y, o.z, c.x, c.y, c.z));
+            s_thr[k] = 4.f * (r * r * 1.001f + 1e-3f);
+            s_c[k] = make_float4(c.x, c.y, c.z, 0.f);
+        }
+        __syncthreads();
         if (s_stop) break;
-        build_rows(P, s_c, s_key, s_rank);
+        build_rows(P, s_c, s_thr, s_key, s_rank, s_cnt);
         if (!grid_sync(P.ctrl, G)) return;
     }
 
@@ -406,7 +469,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
 }
 #undef WSM_VISIT
 
-static size_t sortmeans_smem(int K) { return (size_t)K * (16 + 16 + 8 + 4); }
+static size_t sortmeans_smem(int K) { return (size_t)K * (16 + 16 + 8 + 20 + 4 + 4); }
 
 // Co-residency of the persistent kernel: blocks per SM for the largest K.
 int iterate_kernel_setup(wsm_handle* h) {
@@ -548,7 +611,7 @@ constexpr int kStaticMaxK = WSM_MAX_K;
 constexpr int kStaticMaxGrid = 1024;           // co-resident blocks used at most
 constexpr size_t kStaticTabBytes = sizeof(float4) * kStaticMaxK * kStaticMaxK;   // 1 MiB
 constexpr size_t kStaticNbBytes = (size_t)kStaticMaxK * kStaticMaxK;            // 64 KiB
-constexpr size_t kStaticSumsBytes = sizeof(unsigned) * 2 * kCopies * 4 * kStaticMaxK;
+constexpr size_t kStaticSumsBytes = sizeof(unsigned) * 2 * kCopies * 5 * kStaticMaxK;
 constexpr size_t kStaticSums64Bytes = sizeof(unsigned long long) * 2 * kCopies * 4;
 constexpr size_t kStaticAccBytes = sizeof(unsigned long long) * 4 * kStaticMaxK;
 constexpr size_t kStaticTraceBytes = sizeof(double) * kMaxTrace;
