@@ -44,8 +44,10 @@ H = W = 512
 METRIC = "unique-color assignments/s per iter (K=256) vs FP32 peak; 512² images/s end-to-end"
 UNIT = "assignments/s"
 L2_FLUSH_BYTES = 256 << 20
-KERNELS_PER_IMAGE = 9   # hist24, scan_count, scan_emit, init, sortmeans, sortmeans(map),
-#                         gather, mse_partial, mse_final
+# per image: hist24, scan_count, scan_emit, init, mse_partial, mse_final; per step:
+# the batched sort-means launch, the batched map launch and the batched gather
+KERNELS_PER_IMAGE = 6
+KERNELS_PER_STEP = 3
 
 
 def workload(rank: int):
@@ -198,6 +200,7 @@ def run_gpu(args):
     d_imgs = [torch.from_numpy(im).to(dev) for im in images]
     h_imgs = [torch.from_numpy(im).pin_memory() for im in images]
     handle = wsm.Handle(K_PALETTE, n, n)
+    wsm.wsm_reserve_batch(handle, len(images))
     colors = [torch.empty(n, dtype=torch.uint32, device=dev) for _ in images]
     counts = [torch.empty(n, dtype=torch.uint32, device=dev) for _ in images]
     centers = [torch.empty((K_PALETTE, 4), dtype=torch.float32, device=dev) for _ in images]
@@ -205,25 +208,31 @@ def run_gpu(args):
     index = [torch.empty((H, W), dtype=torch.uint8, device=dev) for _ in images]
     mse = torch.empty(len(images), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    it_events = []          # (start, end) around every persistent iterate launch
+    it_events = []          # (tag, start, end) around every batched iterate launch
     n_unique = [0] * len(images)
 
     def step(record: bool):
+        # a1, a2 per image; a3-a6 for all images in one persistent launch;
+        # a7 for all images in one persistent launch + one gather; a8 per image
+        items = []
         for s, img in enumerate(d_imgs):
             nu = wsm.wsm_reduce(handle, img, colors[s], counts[s])
             n_unique[s] = nu
             wsm.wsm_init(handle, colors[s], nu, K_PALETTE, image_seed(rank, s), centers[s],
                          labels[s])
-            if record:
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            wsm.wsm_iterate(handle, colors[s], counts[s], nu, K_PALETTE, centers[s], labels[s],
-                            ITERS, 0.0, sync=False)
-            if record:
-                e1.record(stream)
-                it_events.append((s, e0, e1))
-            wsm.wsm_map(handle, img, colors[s], nu, centers[s], K_PALETTE, labels[s], index[s])
+            items.append(dict(rgb=img, colors=colors[s], counts=counts[s], n_unique=nu,
+                              K=K_PALETTE, centers=centers[s], labels=labels[s],
+                              index=index[s]))
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        wsm.wsm_iterate_batch(handle, items, ITERS, 0.0, sync=False)
+        if record:
+            e1.record(stream)
+            it_events.append((-1, e0, e1))
+        wsm.wsm_map_batch(handle, items)
+        for s, img in enumerate(d_imgs):
             wsm.wsm_distortion(handle, img, centers[s], K_PALETTE, index[s], d_mse=mse[s:s + 1],
                                sync=False)
 
@@ -271,10 +280,10 @@ def run_gpu(args):
     out_mse = torch.empty(len(images), dtype=torch.float64).pin_memory()
 
     def e2e_step():
-        for s, himg in enumerate(h_imgs):
-            img = himg.to(dev, non_blocking=True)
-            q = wsm.quantize(img, K_PALETTE, seed=image_seed(rank, s), max_iter=ITERS, eps=0.0,
-                             handle=handle, mse=False)
+        imgs = [himg.to(dev, non_blocking=True) for himg in h_imgs]
+        qs = wsm.quantize_batch(imgs, K_PALETTE, [image_seed(rank, s) for s in range(len(imgs))],
+                                max_iter=ITERS, eps=0.0, handle=handle, mse=False)
+        for s, (img, q) in enumerate(zip(imgs, qs)):
             wsm.wsm_distortion(handle, img, q.centers, K_PALETTE, q.index, d_mse=mse[s:s + 1],
                                sync=False)
             out_idx[s].copy_(q.index, non_blocking=True)
@@ -300,7 +309,7 @@ def run_gpu(args):
 
     # roofline of the persistent sort-means kernel, from the timed steps
     it_ms = [e0.elapsed_time(e1) for _, e0, e1 in it_events]
-    it_flop = [8.0 * evaluated[s] for s, _, _ in it_events]
+    it_flop = [8.0 * sum(evaluated) for _ in it_events]   # one launch covers all images
     achieved_tflops = sum(it_flop) / (sum(it_ms) * 1e-3) / 1e12
     pk, pk_kind = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -336,7 +345,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "roofline": {"bound": "alu", "kernel": "k_sortmeans<iterate>",
+            "roofline": {"bound": "alu", "kernel": "k_sortmeans<iterate> (8 images per launch)",
                          "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved_tflops / fp32_peak, "traffic": None,
                          "peak_kind": f"FP32 {sms} SMs x 128 x 2 x {pk.get('sm_max_mhz')} MHz "
@@ -345,7 +354,7 @@ def run_gpu(args):
                          "flop_per_launch": sum(it_flop) / len(it_flop)},
             "cpu_baseline": cpu,
             "clocks": clk,
-            "gpu_launches": KERNELS_PER_IMAGE * len(images) * args.steps,
+            "gpu_launches": (KERNELS_PER_IMAGE * len(images) + KERNELS_PER_STEP) * args.steps,
         }
         print(json.dumps(line), flush=True)
     handle.close()

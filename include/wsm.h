@@ -163,6 +163,47 @@ WSM_API int wsm_iterate(wsm_handle* h, const uint32_t* d_colors, const uint32_t*
 WSM_API int wsm_iterate_stats(wsm_handle* h, int K, int64_t* evaluated, int64_t* S, int64_t* W,
                       wsm_stream stream);
 
+/* One image of a batch call (wsm_iterate_batch, wsm_map_batch); fields as for
+ * the single-image calls.  d_rgb, n_pixels, pixel_stride and d_index are
+ * used by wsm_map_batch only, d_counts by wsm_iterate_batch only. */
+typedef struct {
+    const uint8_t* d_rgb;       /* [n_pixels][pixel_stride] */
+    int64_t n_pixels;
+    int pixel_stride;           /* 3 or 4 */
+    int K;                      /* 1 <= K <= max_K */
+    const uint32_t* d_colors;   /* [n_unique] ascending */
+    const uint32_t* d_counts;   /* [n_unique] */
+    int64_t n_unique;
+    float* d_centers;           /* [K][4], 16-byte aligned */
+    uint8_t* d_labels;          /* [n_unique] */
+    uint8_t* d_index;           /* [n_pixels] */
+} wsm_item;
+
+/* Reserve per-image scratch for batches of up to max_items images (about
+ * 17.2 MiB each at max_K = 256, dominated by the color->label table).
+ * Synchronises the device.  A new handle has one slot.
+ * Errors: WSM_E_INVAL, WSM_E_NOMEM (the handle keeps one slot). */
+WSM_API int wsm_reserve_batch(wsm_handle* h, int max_items);
+
+/* Algorithm 2 with the Sec. 3.2 termination rule for n_items independent
+ * images in one persistent cooperative launch per 48 images: the blocks are
+ * split into one group per image (in proportion to its unique colors and
+ * palette size), each group iterating its image exactly as wsm_iterate would
+ * (same results, bit for bit) with a barrier of its own, so images of
+ * different sizes and iteration counts share the launch.  Each item needs
+ * d_colors, d_counts, n_unique, K, d_centers, d_labels.
+ *   iters_done  host int [n_items] (may be NULL; if given, synchronises)
+ * Errors: WSM_E_INVAL (item sizes, more items than reserved slots),
+ * WSM_E_TIMEOUT. */
+WSM_API int wsm_iterate_batch(wsm_handle* h, const wsm_item* items, int n_items, int max_iter,
+                              double eps, int* iters_done, wsm_stream stream);
+
+/* Sec. 1, pixel mapping for n_items images: one final pruned assignment per
+ * image in one persistent launch (as wsm_map), then one gather launch over
+ * all images' pixels.  Each item needs every field but d_counts.
+ * Errors: as wsm_map. */
+WSM_API int wsm_map_batch(wsm_handle* h, const wsm_item* items, int n_items, wsm_stream stream);
+
 /* Allocation-free variant of wsm_iterate.  The paper has no counterpart:
  * it exists for callers that cannot call cudaMalloc -- a plugin inside a
  * host program that owns every device byte through its own pool, a process

@@ -28,6 +28,14 @@ _lib = None
 _P = C.c_void_p
 _I64 = C.c_int64
 
+class WsmItem(C.Structure):
+    """wsm_item of include/wsm.h: one image of a batch call."""
+    _fields_ = [("d_rgb", C.c_void_p), ("n_pixels", C.c_int64), ("pixel_stride", C.c_int),
+                ("K", C.c_int), ("d_colors", C.c_void_p), ("d_counts", C.c_void_p),
+                ("n_unique", C.c_int64), ("d_centers", C.c_void_p), ("d_labels", C.c_void_p),
+                ("d_index", C.c_void_p)]
+
+
 SIGNATURES = {
     "wsm_last_error": (C.c_char_p, []),
     "wsm_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _I64, _I64]),
@@ -41,6 +49,9 @@ SIGNATURES = {
     "wsm_iterate_noalloc": (C.c_int, [_P, _P, _I64, C.c_int, _P, _P, C.c_int, C.c_double,
                                       C.POINTER(C.c_int), _P, _P]),
     "wsm_map": (C.c_int, [_P, _P, _I64, C.c_int, _P, _I64, _P, C.c_int, _P, _P, _P]),
+    "wsm_reserve_batch": (C.c_int, [_P, C.c_int]),
+    "wsm_iterate_batch": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_double, _P, _P]),
+    "wsm_map_batch": (C.c_int, [_P, _P, C.c_int, _P]),
     "wsm_distortion": (C.c_int, [_P, _P, _I64, C.c_int, _P, C.c_int, _P, _P,
                                  C.POINTER(C.c_double), _P]),
 }
@@ -216,6 +227,49 @@ def wsm_map(h: Handle, rgb: torch.Tensor, colors: torch.Tensor, n_unique: int,
                          _dev(centers, torch.float32, "centers", 4 * K), K,
                          _dev(labels, torch.uint8, "labels", n_unique),
                          _dev(index, torch.uint8, "index", n), _stream(stream)))
+
+
+def wsm_reserve_batch(h: Handle, max_items: int):
+    _check(lib().wsm_reserve_batch(h.ptr, int(max_items)))
+
+
+def _items(images: list[dict], need_pixels: bool, need_counts: bool):
+    """Marshal dicts with tensors (rgb, colors, counts, n_unique, K, centers,
+    labels, index) into a wsm_item array."""
+    arr = (WsmItem * max(len(images), 1))()
+    for q, im in enumerate(images):
+        K, nu = int(im["K"]), int(im["n_unique"])
+        it = arr[q]
+        it.K = K
+        it.n_unique = nu
+        it.d_colors = _dev(im["colors"], torch.uint32, "colors", nu)
+        it.d_centers = _dev(im["centers"], torch.float32, "centers", 4 * K)
+        it.d_labels = _dev(im["labels"], torch.uint8, "labels", nu)
+        if need_counts:
+            it.d_counts = _dev(im["counts"], torch.uint32, "counts", nu)
+        if need_pixels:
+            n, stride = _pixels(im["rgb"])
+            it.d_rgb = _dev(im["rgb"], torch.uint8, "rgb")
+            it.n_pixels = n
+            it.pixel_stride = stride
+            it.d_index = _dev(im["index"], torch.uint8, "index", n)
+    return arr
+
+
+def wsm_iterate_batch(h: Handle, images: list[dict], max_iter: int, eps: float,
+                      sync: bool = True, stream=None):
+    """Iterate every image of the batch; returns the iteration counts if sync."""
+    arr = _items(images, False, True)
+    done = (C.c_int * max(len(images), 1))()
+    _check(lib().wsm_iterate_batch(h.ptr, C.cast(arr, C.c_void_p), len(images), max_iter,
+                                   float(eps), C.cast(done, C.c_void_p) if sync else None,
+                                   _stream(stream)))
+    return [done[i] for i in range(len(images))] if sync else None
+
+
+def wsm_map_batch(h: Handle, images: list[dict], stream=None):
+    arr = _items(images, True, False)
+    _check(lib().wsm_map_batch(h.ptr, C.cast(arr, C.c_void_p), len(images), _stream(stream)))
 
 
 def wsm_distortion(h: Handle, rgb: torch.Tensor, centers: torch.Tensor, K: int,

@@ -95,6 +95,58 @@ __global__ void k_init(const uint32_t* __restrict__ colors, int64_t n_unique, in
 
 int iterate_kernel_setup(wsm_handle* h);   // wsm_iterate.cu
 
+void free_slots(wsm_handle* h) {
+    void* ptrs[] = {h->tab, h->tab_nb, h->sums, h->sums64, h->acc, h->trace, h->lut,
+                    h->slot_ctrl};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    h->tab = nullptr;
+    h->tab_nb = nullptr;
+    h->sums = nullptr;
+    h->sums64 = nullptr;
+    h->acc = nullptr;
+    h->trace = nullptr;
+    h->lut = nullptr;
+    h->slot_ctrl = nullptr;
+    h->slots = 0;
+}
+
+// Per-image scratch for `slots` images (replaces any previous slots).
+int alloc_slots(wsm_handle* h, int slots) {
+    free_slots(h);
+    const size_t kk = (size_t)h->max_K * h->max_K, n = (size_t)slots;
+    struct {
+        void** p;
+        size_t bytes;
+    } allocs[] = {
+        {(void**)&h->tab, sizeof(float4) * kk * n},
+        {(void**)&h->tab_nb, kk * n},
+        {(void**)&h->sums, sizeof(unsigned) * 2 * kCopies * 5 * (size_t)h->max_K * n},
+        {(void**)&h->sums64, sizeof(unsigned long long) * 2 * kCopies * 4 * n},
+        {(void**)&h->acc, sizeof(unsigned long long) * 4 * (size_t)h->max_K * n},
+        {(void**)&h->trace, sizeof(double) * kMaxTrace * n},
+        {(void**)&h->lut, (size_t)kHistBins * n},
+        {(void**)&h->slot_ctrl, sizeof(Ctrl) * n},
+    };
+    for (auto& a : allocs) {
+        cudaError_t e = cudaMalloc(a.p, a.bytes);
+        if (e != cudaSuccess) {
+            free_slots(h);
+            return fail(WSM_E_NOMEM, std::string("cudaMalloc (image slots): ") +
+                                         cudaGetErrorString(e));
+        }
+    }
+    cudaError_t e = cudaMemset(h->slot_ctrl, 0, sizeof(Ctrl) * n);
+    if (e == cudaSuccess)
+        e = cudaMemset(h->acc, 0, sizeof(unsigned long long) * 4 * (size_t)h->max_K * n);
+    if (e != cudaSuccess) {
+        free_slots(h);
+        return cuda_fail(e, "slot initialisation");
+    }
+    h->slots = slots;
+    return WSM_OK;
+}
+
 }  // namespace wsm
 
 using namespace wsm;
@@ -126,7 +178,6 @@ extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64
         delete h;
         return rc;
     }
-    size_t kk = (size_t)max_K * max_K;
     struct {
         void** p;
         size_t bytes;
@@ -134,13 +185,6 @@ extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64
         {(void**)&h->hist, sizeof(uint32_t) * kHistBins},
         {(void**)&h->bitmap, sizeof(uint32_t) * kMapWords},
         {(void**)&h->blk_total, sizeof(uint32_t) * kScanBlocks},
-        {(void**)&h->lut, (size_t)kHistBins},
-        {(void**)&h->tab, sizeof(float4) * kk},
-        {(void**)&h->tab_nb, kk},
-        {(void**)&h->sums, sizeof(unsigned) * 2 * kCopies * 5 * (size_t)max_K},
-        {(void**)&h->sums64, sizeof(unsigned long long) * 2 * kCopies * 4},
-        {(void**)&h->acc, sizeof(unsigned long long) * 4 * max_K},
-        {(void**)&h->trace, sizeof(double) * kMaxTrace},
         {(void**)&h->mse_part, sizeof(double) * 1032},   // 1024 partials + result
         {(void**)&h->ctrl, sizeof(Ctrl)},
     };
@@ -151,6 +195,11 @@ extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64
             return fail(WSM_E_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         }
     }
+    rc = alloc_slots(h, 1);
+    if (rc != WSM_OK) {
+        wsm_destroy(h);
+        return rc;
+    }
     e = cudaMallocHost((void**)&h->host_ctrl, sizeof(Ctrl));
     if (e != cudaSuccess) {
         wsm_destroy(h);
@@ -159,7 +208,6 @@ extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64
     e = cudaMemset(h->hist, 0, sizeof(uint32_t) * kHistBins);
     if (e == cudaSuccess) e = cudaMemset(h->bitmap, 0, sizeof(uint32_t) * kMapWords);
     if (e == cudaSuccess) e = cudaMemset(h->ctrl, 0, sizeof(Ctrl));
-    if (e == cudaSuccess) e = cudaMemset(h->acc, 0, sizeof(unsigned long long) * 4 * max_K);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         wsm_destroy(h);
@@ -175,13 +223,29 @@ extern "C" int wsm_destroy(wsm_handle* h) {
     cudaGetDevice(&prev);
     if (h->device >= 0 && prev != h->device) cudaSetDevice(h->device);
     cudaDeviceSynchronize();
-    void* dev_ptrs[] = {h->hist, h->bitmap, h->blk_total, h->lut, h->tab, h->tab_nb, h->sums,
-                        h->sums64, h->acc, h->trace, h->mse_part, h->ctrl};
+    free_slots(h);
+    void* dev_ptrs[] = {h->hist, h->bitmap, h->blk_total, h->mse_part, h->ctrl};
     for (void* p : dev_ptrs)
         if (p) cudaFree(p);
     if (h->host_ctrl) cudaFreeHost(h->host_ctrl);
     if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
     delete h;
+    return WSM_OK;
+}
+
+extern "C" int wsm_reserve_batch(wsm_handle* h, int max_items) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (max_items < 1 || max_items > 4096) return fail(WSM_E_INVAL, "max_items must be in [1, 4096]");
+    if (max_items <= h->slots) return WSM_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "device sync");
+    rc = alloc_slots(h, max_items);
+    if (rc != WSM_OK) {
+        int rc1 = alloc_slots(h, 1);   // keep the handle usable for single images
+        (void)rc1;
+        return rc;
+    }
     return WSM_OK;
 }
 

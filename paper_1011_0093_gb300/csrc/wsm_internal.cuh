@@ -32,6 +32,7 @@ constexpr int kIterThreads = 512;            // threads per block of the persist
 constexpr int kMaxTrace = 4096;              // SSE values kept per wsm_iterate call
 constexpr int kCopies = 8;                   // replicas of the global accumulators
 constexpr int kChunk = 32;                   // colors per warp chunk (one per lane)
+constexpr int kMaxBatch = 48;                // images per persistent launch
 
 // Control words in device memory (one block per handle).
 // The fields before `status` are cleared before every persistent launch, so
@@ -62,16 +63,19 @@ struct wsm_handle {
     uint32_t* hist = nullptr;    // [2^24] zero between calls
     uint32_t* bitmap = nullptr;  // [2^19] zero between calls
     uint32_t* blk_total = nullptr;   // [kScanBlocks]
-    uint8_t* lut = nullptr;      // [2^24] color -> label
-    float4* tab = nullptr;       // [max_K * max_K] sorted rows: (d/4, c.x, c.y, c.z)
-    uint8_t* tab_nb = nullptr;   // [max_K * max_K] center index of each row entry
-    unsigned* sums = nullptr;    // [2][kCopies][5 max_K] replicated cluster sums and maxima
-    unsigned long long* sums64 = nullptr;  // [2][kCopies][4] SSE, distances, pixels, nonzero
-    unsigned long long* acc = nullptr;  // [max_K][4]: S_k (3) and W_k of the last pass
-    double* trace = nullptr;     // [kMaxTrace]
     double* mse_part = nullptr;  // [1024] block partials + [1] result
-    wsm::Ctrl* ctrl = nullptr;
+    wsm::Ctrl* ctrl = nullptr;   // status word, N', MSE mirror
     wsm::Ctrl* host_ctrl = nullptr;  // pinned mirror for status reads
+    // per-image scratch of the persistent kernel, one slot per image of a batch
+    int slots = 0;
+    float4* tab = nullptr;       // [slots][max_K^2] sorted rows: (d/4, c.x, c.y, c.z)
+    uint8_t* tab_nb = nullptr;   // [slots][max_K^2] center index of each row entry
+    unsigned* sums = nullptr;    // [slots][2][kCopies][5 max_K] replicated sums and maxima
+    unsigned long long* sums64 = nullptr;  // [slots][2][kCopies][4] SSE, distances, pixels, nonzero
+    unsigned long long* acc = nullptr;     // [slots][4 max_K] S_k (3) and W_k of the last pass
+    double* trace = nullptr;     // [slots][kMaxTrace]
+    uint8_t* lut = nullptr;      // [slots][2^24] color -> label
+    wsm::Ctrl* slot_ctrl = nullptr;  // [slots] barrier counter, iterations, distances
 };
 
 namespace wsm {
@@ -81,6 +85,8 @@ int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 int check_handle(wsm_handle* h);
 int read_status(wsm_handle* h, cudaStream_t s);
+int alloc_slots(wsm_handle* h, int slots);
+void free_slots(wsm_handle* h);
 
 // ---------------------------------------------------------------------------
 // Device helpers
@@ -104,25 +110,25 @@ __device__ __forceinline__ unsigned add_release(unsigned* p, unsigned v) {
     return old;
 }
 
-// Grid-wide barrier for a cooperative launch of `nblocks` co-resident blocks.
-// Thread 0 of each block adds 1 to a counter that only grows (release), and
-// waits (acquire) until it reaches the next multiple of nblocks, i.e. until
-// every block has arrived at this barrier.  The wait has a time limit: past
-// it the status word gets ST_TIMEOUT and the function returns false in every
-// thread of the block.  Memory written before the barrier by any block is
-// visible to every block after it.
-__device__ __forceinline__ bool grid_sync(Ctrl* ctrl, unsigned nblocks) {
+// Barrier over `nblocks` co-resident blocks (a whole cooperative grid, or one
+// image's group of it).  Thread 0 of each block adds 1 to a counter that only
+// grows (release), and waits (acquire) until it reaches the next multiple of
+// nblocks, i.e. until every block has arrived at this barrier.  The wait has
+// a time limit: past it *status gets ST_TIMEOUT and the function returns false
+// in every thread of the block.  Memory written before the barrier by any of
+// the blocks is visible to all of them after it.
+__device__ __forceinline__ bool grid_sync(unsigned* counter, unsigned* status, unsigned nblocks) {
     __shared__ unsigned s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned old = add_release(&ctrl->bar_count, 1u);
+        unsigned old = add_release(counter, 1u);
         unsigned target = (old / nblocks + 1u) * nblocks;
         unsigned ok = 1u;
-        if ((int)(ld_acquire(&ctrl->bar_count) - target) < 0) {
+        if ((int)(ld_acquire(counter) - target) < 0) {
             unsigned long long t0 = global_ns();
-            while ((int)(ld_acquire(&ctrl->bar_count) - target) < 0) {
+            while ((int)(ld_acquire(counter) - target) < 0) {
                 if (global_ns() - t0 > kWaitLimitNs) {
-                    atomicOr(&ctrl->status, ST_TIMEOUT);
+                    atomicOr(status, ST_TIMEOUT);
                     ok = 0u;
                     break;
                 }

@@ -1,65 +1,88 @@
 // wsm_iterate.cu -- the Sort-Means loop of Algorithm 2 (Sec. 2) as one
-// persistent cooperative kernel, used both for the iterations (wsm_iterate)
-// and for the final assignment before pixel mapping (wsm_map).
+// persistent cooperative kernel over a batch of images, used for the
+// iterations (wsm_iterate, wsm_iterate_batch) and for the final assignment
+// before pixel mapping (wsm_map, wsm_map_batch).
 //
-// One launch runs every iteration, as two phases separated by grid barriers:
-//   A  every block turns the cluster sums of the previous pass into the new
-//      centers c_k = S_k / W_k (correctly rounded to FP32; an empty cluster
-//      keeps its center), measures that pass's SSE and applies the Sec. 3.2
-//      stop rule (all blocks compute the same values, so all decide alike),
-//      then sorts rows p = b, b+G, ... of the center table: row p lists,
-//      nearest first, the entries (d[p][t] / 4, c_t) for the centers t, ties
-//      ordered by (t != p, t), so entry 0 is p itself.  In the first pass of
-//      a launch a row holds every center; later a row holds only the centers
-//      below a bound that no visit of that row can pass (see the row bound
-//      below), followed by entries with an infinite bound -- the entries a
-//      visit reads, and their order, are the same as with the full row.
+// The blocks of a launch are split into one group per image (sized by the
+// image's unique colors and palette); a group runs its image on its own, with
+// a grid barrier of its own, so images of different sizes and iteration
+// counts share one launch.  Within a group:
+//   0  bound pass: every color's squared distance to its current center,
+//      prev = ||x - c_p||^2, raises the largest prev of cluster p;
+//   A  block b of the group (of G) turns the cluster sums of the previous
+//      pass into the new centers c_k = S_k / W_k (correctly rounded to FP32;
+//      an empty cluster keeps its center), measures that pass's SSE and
+//      applies the Sec. 3.2 stop rule (all blocks compute the same values,
+//      so all decide alike); then the warps build rows p = b, b + G, ... of
+//      the center table: row p lists, nearest first, the entries
+//      (d[p][t] / 4, c_t), ties ordered by (t != p, t), so entry 0 is p.
+//      A row keeps only the centers t with d[p][t] below four times a bound
+//      on the prev of any member of cluster p -- no visit of row p goes
+//      further (Sec. 2: the visit stops at d[p][t] >= 4 prev) -- followed by
+//      four entries with an infinite bound; the entries a visit reads, and
+//      their order, are those of the full row.  The bound is the largest
+//      prev of the bound pass for the first table, and afterwards
+//      (sqrt(largest min_dist of the pass) + ||c_p,new - c_p,old||)^2 by the
+//      triangle inequality, with a margin for FP32 rounding.
 //   B  the pruned nearest-center search, one lane per unique color; warp w
 //      of block b takes the chunks of 32 consecutive colors numbered
-//      b * WPB + w + k * G * WPB (spreading costly regions of color space over
-//      all blocks) and loads the next chunk's records while it searches the
-//      current one.  A color starts at its previous center p with
-//      prev = ||x - c_p||^2 and visits row p from entry 1 on; the visit stops
-//      at the first entry with d[p][t] / 4 >= prev (the paper's
-//      d[p][t] >= 4 prev_dist; scaling by 4 is exact), and a visited center
-//      replaces the current one when its distance is <= the running
-//      minimum, so among equal distances the one visited last wins.  Entries
-//      are loaded four at a time; since a row is sorted, the four are all
-//      visited when the last one is below the bound.  Cluster sums are
-//      accumulated per block in shared memory (uint32, exact because an
-//      image has at most 2^24 pixels) and added into one of kCopies
-//      replicated global accumulators (integer atomics, so the totals are
-//      exact and independent of the order).
+//      b * WPB + w + k * G * WPB and loads the next chunk's records while it
+//      searches the current one.  A color starts at its previous center p
+//      and visits row p from entry 1 on; the visit stops at the first entry
+//      with d[p][t] / 4 >= prev (the paper's d[p][t] >= 4 prev_dist; scaling
+//      by 4 is exact), and a visited center replaces the current one when its
+//      distance is <= the running minimum, so among equal distances the one
+//      visited last wins.  Entries are loaded four at a time; a row is
+//      sorted, so when the last of four is below the bound all four are
+//      visited.  Cluster sums (uint32, exact because an image has at most
+//      2^24 pixels) are accumulated per block in shared memory and added into
+//      one of kCopies replicated global accumulators (integer atomics: the
+//      totals are exact and independent of the order).
 // The SSE is accumulated as an integer in units of 2^-20 (each color's
 // n_i * min_dist_i truncated to that grid), so every reduction is exact and
-// the results do not depend on the grid or on the order of the additions.
+// the results do not depend on the grid, the grouping or the order.
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "wsm_internal.cuh"
 
 namespace wsm {
 
-struct SortMeansParams {
-    const uint32_t* colors;
-    const uint32_t* counts;
+// One image of a launch.
+struct ItemDesc {
+    const uint32_t* colors;    // [n] ascending 0xRRGGBB
+    const uint32_t* counts;    // [n]
+    uint8_t* labels;           // [n] in/out
+    float4* centers;           // [K] in/out (read-only in the map mode)
     int64_t n;
     int K;
-    float4* centers;       // [K] in/out (read-only in the map mode)
-    uint8_t* labels;       // [n] in/out
+    int slot;                  // scratch slot
+};
+
+// Per-image scratch: slot s of each array starts at base + s * (its slot size).
+struct Scratch {
+    float4* tab;               // [max_K^2] rows of (d/4, c.x, c.y, c.z), nearest first
+    uint8_t* tab_nb;           // [max_K^2] center index of each entry
+    unsigned* sums;            // [2][kCopies][5 max_K] cluster sums (4K) and the largest
+                               //   prev / min_dist of a member (K, FP32 bits), by pass parity
+    unsigned long long* sums64;    // [2][kCopies][4] SSE (2^-20 units), distances, pixels,
+                                   //   colors with a nonzero minimum
+    unsigned long long* acc;   // [4 max_K] cluster sums of the last pass
+    double* trace;             // [kMaxTrace]
+    uint8_t* lut;              // [2^24] color -> label (map mode)
+    Ctrl* ctrl;                // barrier counter, iterations, distances
+    int max_K;
+};
+
+struct BatchParams {
+    Scratch sc;
+    unsigned* status;          // ST_* bits for the whole call
+    int n_items;
     int max_iter;
     double eps;
-    float4* tab;           // [K*K] rows of (d/4, c.x, c.y, c.z), nearest first
-    uint8_t* tab_nb;       // [K*K] center index of each entry
-    unsigned* sums;        // [2][kCopies][5K] cluster sums (4K) and the largest squared
-                           //   distance of a member to its center (K, FP32 bits),
-                           //   double-buffered by pass parity
-    unsigned long long* sums64;  // [2][kCopies][4] SSE (2^-20 units), distances, pixels,
-                                 //   colors with a nonzero minimum
-    unsigned long long* acc;     // [K][4] cluster sums of the last pass
-    double* trace;         // [kMaxTrace]
-    uint8_t* lut;          // map mode: [2^24] color -> label
-    Ctrl* ctrl;
+    int first_blk[kMaxBatch + 1];  // image i owns blocks [first_blk[i], first_blk[i+1])
+    ItemDesc item[kMaxBatch];
 };
 
 // floor(t / W) for t < 128 W (or t < 2^32 with a quotient below 2^8) and
@@ -125,22 +148,22 @@ __device__ __forceinline__ unsigned long long row_key(float d, int t, int p) {
     return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(t == p ? 0 : t + 1);
 }
 
-// This block's rows of the sorted center table.  Row p keeps the centers t
-// with d[p][t] < thr[p] (p itself always), sorted by rank: the rank of a key
-// among the kept keys (keys are distinct) is its entry position, S threads
-// share one key's comparisons.  Four entries with an infinite bound follow
-// the kept ones, so every visit stops there (the scan reads four entries per
-// step).  thr = NULL keeps every center.
-__device__ __forceinline__ void build_rows(const SortMeansParams& P, const float4* s_c,
-                                           const float* thr, unsigned long long* s_key,
-                                           int* s_rank, int* s_cnt) {
-    const int K = P.K, tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
-    for (int p = blockIdx.x; p < K; p += gridDim.x) {
+// The rows p = b, b + G, ... of one image's table, one row per warp at a time.
+// Row p keeps the centers t with d[p][t] < thr[p] (p itself always); the
+// rank of a key among the kept keys (keys are distinct) is its entry
+// position.  Four entries with an infinite bound follow the kept ones.
+__device__ __forceinline__ void build_rows(int K, int G, int b, const float4* s_c,
+                                           const float* s_thr, unsigned long long* s_wkey,
+                                           float4* tab, uint8_t* tab_nb) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, WPB = blockDim.x >> 5;
+    unsigned long long* key = s_wkey + (size_t)wid * K;        // this warp's buffer
+    const unsigned below = (1u << lane) - 1u;
+    for (int p = b + wid * G; p < K; p += G * WPB) {
         const float4 cp = s_c[p];
-        const float bound = thr ? thr[p] : __int_as_float(0x7f800000);
-        // kept centers, compacted in index order (K <= 256 <= T: one round)
-        {
-            const int t = tid;
+        const float bound = s_thr[p];
+        int L = 0;
+        for (int t0 = 0; t0 < K; t0 += 32) {
+            const int t = t0 + lane;
             float d = 0.f;
             bool keep = false;
             if (t < K) {
@@ -149,49 +172,26 @@ __device__ __forceinline__ void build_rows(const SortMeansParams& P, const float
                 keep = d < bound || t == p;
             }
             const unsigned vote = __ballot_sync(0xFFFFFFFFu, keep);
-            if (lane == 0) s_cnt[wid] = __popc(vote);
-            __syncthreads();
-            if (tid == 0) {
-                int run = 0;
-                for (int w = 0; w < (T >> 5); ++w) {
-                    const int c = s_cnt[w];
-                    s_cnt[w] = run;
-                    run += c;
-                }
-                s_cnt[32] = run;
-            }
-            __syncthreads();
-            if (keep) s_key[s_cnt[wid] + __popc(vote & ((1u << lane) - 1u))] = row_key(d, t, p);
-            if (tid < K) s_rank[tid] = 0;
-            __syncthreads();
+            if (keep) key[L + __popc(vote & below)] = row_key(d, t, p);
+            L += __popc(vote);
         }
-        const int L = s_cnt[32];
-        const int S = max(1, T / L);
-        const int span = (L + S - 1) / S;
-        for (int t = tid; t < S * L; t += T) {
-            const int j = t % L, h = t / L;
-            const unsigned long long kj = s_key[j];
-            const int lo = h * span, hi = min(L, lo + span);
+        __syncwarp();
+        float4* row = tab + (size_t)p * K;
+        uint8_t* row_nb = tab_nb + (size_t)p * K;
+        for (int j = lane; j < L; j += 32) {
+            const unsigned long long kj = key[j];
             int rank = 0;
 #pragma unroll 8
-            for (int k = lo; k < hi; ++k) rank += s_key[k] < kj;
-            if (S == 1) s_rank[j] = rank;
-            else if (rank) atomicAdd(s_rank + j, rank);
-        }
-        __syncthreads();
-        for (int t = tid; t < L; t += T) {
-            const unsigned long long key = s_key[t];
-            const unsigned lo = (unsigned)key;
+            for (int k = 0; k < L; ++k) rank += key[k] < kj;
+            const unsigned lo = (unsigned)kj;
             const int c = lo ? (int)lo - 1 : p;
             const float4 ct = s_c[c];
-            const int r = s_rank[t];
-            P.tab[(size_t)p * K + r] =
-                make_float4(__uint_as_float((unsigned)(key >> 32)) * 0.25f, ct.x, ct.y, ct.z);
-            P.tab_nb[(size_t)p * K + r] = (uint8_t)c;
+            row[rank] = make_float4(__uint_as_float((unsigned)(kj >> 32)) * 0.25f, ct.x, ct.y, ct.z);
+            row_nb[rank] = (uint8_t)c;
         }
-        if (tid < 4 && L + tid < K)
-            P.tab[(size_t)p * K + L + tid] = make_float4(__int_as_float(0x7f800000), 0.f, 0.f, 0.f);
-        __syncthreads();
+        if (lane < 4 && L + lane < K)
+            row[L + lane] = make_float4(__int_as_float(0x7f800000), 0.f, 0.f, 0.f);
+        __syncwarp();
     }
 }
 
@@ -206,74 +206,114 @@ __device__ __forceinline__ void build_rows(const SortMeansParams& P, const float
     }
 
 template <bool kMap>
-__global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P) {
-    extern __shared__ float4 smem[];
-    const int K = P.K;
-    float4* s_c = smem;                                                       // [K] centers
-    float4* s_cn = s_c + K;                                                   // [K] new centers
-    unsigned long long* s_key = reinterpret_cast<unsigned long long*>(s_cn + K);  // [K]
-    unsigned* s_acc = reinterpret_cast<unsigned*>(s_key + K);                 // [5K] sums, max
-    float* s_thr = reinterpret_cast<float*>(s_acc + 5 * K);                   // [K] row bounds
-    int* s_rank = reinterpret_cast<int*>(s_thr + K);                          // [K]
-    __shared__ unsigned long long s_red[4][kIterThreads / 32];
-    __shared__ int s_cnt[33];
-    __shared__ int s_stop;
+__global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(const __grid_constant__ BatchParams P) {
+    // ---- this block's image and group
+    int ii = 0;
+    while (ii + 1 < P.n_items && (int)blockIdx.x >= P.first_blk[ii + 1]) ++ii;
+    const ItemDesc I = P.item[ii];
+    const int G = P.first_blk[ii + 1] - P.first_blk[ii];
+    const int b = blockIdx.x - P.first_blk[ii];
+    const int K = I.K;
+    const int64_t n = I.n;
+    const size_t kk = (size_t)P.sc.max_K * P.sc.max_K, s5 = (size_t)5 * P.sc.max_K;
+    float4* const tab = P.sc.tab + (size_t)I.slot * kk;
+    uint8_t* const tab_nb = P.sc.tab_nb + (size_t)I.slot * kk;
+    unsigned* const sums = P.sc.sums + (size_t)I.slot * 2 * kCopies * s5;
+    unsigned long long* const sums64 = P.sc.sums64 + (size_t)I.slot * 2 * kCopies * 4;
+    unsigned long long* const acc = P.sc.acc + (size_t)I.slot * 4 * P.sc.max_K;
+    double* const trace = P.sc.trace + (size_t)I.slot * kMaxTrace;
+    uint8_t* const lut = kMap ? P.sc.lut + (size_t)I.slot * kHistBins : nullptr;
+    Ctrl* const ctrl = P.sc.ctrl + I.slot;
 
+    extern __shared__ float4 smem[];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int T = blockDim.x, WPB = T >> 5;
-    const int G = gridDim.x, b = blockIdx.x;
+    const int KM = P.sc.max_K;                  // smem arrays are sized for the batch's largest K
+    float4* s_c = smem;                                                       // [KM] centers
+    float4* s_cn = s_c + KM;                                                  // [KM] new centers
+    unsigned* s_acc = reinterpret_cast<unsigned*>(s_cn + KM);                 // [5KM] sums, max
+    float* s_thr = reinterpret_cast<float*>(s_acc + 5 * KM);                  // [KM] row bounds
+    unsigned long long* s_wkey = reinterpret_cast<unsigned long long*>(s_thr + KM);  // [WPB][KM]
+    __shared__ unsigned long long s_red[4][kIterThreads / 32];
+    __shared__ int s_stop;
+
     const int copy = b % kCopies;
-    const int64_t n = P.n;
     if (!kMap && P.max_iter <= 0) return;
 
-    for (int k = tid; k < K; k += T) s_c[k] = P.centers[k];
-    if (!kMap && b == 0) {
-        for (int j = tid; j < kCopies * 5 * K; j += T) P.sums[j] = 0u;
-        if (tid < 4 * kCopies) P.sums64[tid] = 0ull;
-    }
+    // the slot's accumulators (both parities) were cleared before the launch
+    for (int k = tid; k < K; k += T) s_c[k] = I.centers[k];
+    for (int j = tid; j < 5 * K; j += T) s_acc[j] = 0u;
     __syncthreads();
-    build_rows(P, s_c, nullptr, s_key, s_rank, s_cnt);
-    if (!grid_sync(P.ctrl, G)) return;
+
+    // Colors of this block: chunks of kChunk, one per lane, warp w of block b
+    // takes chunks b * WPB + w + m * G * WPB.
+    const int64_t first = ((int64_t)b * WPB + wid) * kChunk;
+    const int64_t stride = (int64_t)G * WPB * kChunk;
+
+    // ---------------- bound pass ----------------
+    {
+        bool bad = false;
+        for (int64_t cur = first; cur < n; cur += stride) {
+            const int64_t i = cur + lane;
+            if (i < n) {
+                const uint32_t col = __ldg(I.colors + i);
+                int p = I.labels[i];
+                if (p >= K) {
+                    bad = true;
+                    p = 0;
+                }
+                const float4 cp = s_c[p];
+                const float prev = sq3((float)((col >> 16) & 255u), (float)((col >> 8) & 255u),
+                                       (float)(col & 255u), cp.x, cp.y, cp.z);
+                atomicMax(s_acc + 4 * K + p, __float_as_uint(prev));
+            }
+        }
+        if (bad) atomicOr(P.status, ST_BAD_LABEL);
+        __syncthreads();
+        unsigned* dst = sums + (size_t)(kCopies + copy) * s5;   // parity 1, zeroed above
+        for (int k = tid; k < K; k += T) {
+            const unsigned v = s_acc[4 * K + k];
+            if (v) atomicMax(dst + 4 * K + k, v);
+        }
+        if (!grid_sync(&ctrl->bar_count, P.status, G)) return;
+        for (int k = tid; k < K; k += T) {
+            unsigned m = 0;
+#pragma unroll
+            for (int c = 0; c < kCopies; ++c) m = max(m, sums[(size_t)(kCopies + c) * s5 + 4 * K + k]);
+            s_thr[k] = 4.f * (__uint_as_float(m) * 1.001f + 1e-3f);
+        }
+        __syncthreads();
+        build_rows(K, G, b, s_c, s_thr, s_wkey, tab, tab_nb);
+        if (!grid_sync(&ctrl->bar_count, P.status, G)) return;
+    }
 
     unsigned long long prev_fx = 0;        // SSE of the previous pass, in thread 0 only
     for (int it = 0;; ++it) {
         // ---------------- phase B: assignment ----------------
         const int buf = it & 1;
-        if (!kMap)
-            for (int j = tid; j < 5 * K; j += T) s_acc[j] = 0u;
+        for (int j = tid; j < 5 * K; j += T) s_acc[j] = 0u;
         __syncthreads();
         unsigned long long sse_fx = 0, ev = 0, npix = 0, nonzero = 0;
         bool bad = false;
-        // Chunks of kChunk consecutive colors, one color per lane: warp w of
-        // block b takes chunks c = b * WPB + w, then c + G * WPB, ...  The next
-        // chunk's records are loaded while the current one is searched.
-#ifdef WSM_CONTIGUOUS
-        const int64_t per_block = (n + G - 1) / G;
-        const int64_t blk_lo = min(n, (int64_t)b * per_block), blk_hi = min(n, blk_lo + per_block);
-        int64_t cur = blk_lo + (int64_t)wid * kChunk;
-        const int64_t stride = (int64_t)WPB * kChunk, lim = blk_hi;
-#else
-        int64_t cur = ((int64_t)b * WPB + wid) * kChunk;
-        const int64_t stride = (int64_t)G * WPB * kChunk, lim = n;
-#endif
+        int64_t cur = first;
         uint32_t col_n = 0, cnt_n = 0;
         int lab_n = 0;
-        if (cur + lane < lim) {
-            col_n = __ldg(P.colors + cur + lane);
-            lab_n = P.labels[cur + lane];
-            if (!kMap) cnt_n = __ldg(P.counts + cur + lane);
+        if (cur + lane < n) {
+            col_n = __ldg(I.colors + cur + lane);
+            lab_n = I.labels[cur + lane];
+            if (!kMap) cnt_n = __ldg(I.counts + cur + lane);
         }
-        for (; cur < lim; cur += stride) {
+        for (; cur < n; cur += stride) {
             const int64_t nxt = cur + stride;
             const int64_t i = cur + lane;
-            const bool active = i < lim;
+            const bool active = i < n;
             const uint32_t col = col_n;
             const unsigned cnt = cnt_n;
             const int p0 = lab_n;
-            if (nxt + lane < lim) {
-                col_n = __ldg(P.colors + nxt + lane);
-                lab_n = P.labels[nxt + lane];
-                if (!kMap) cnt_n = __ldg(P.counts + nxt + lane);
+            if (nxt + lane < n) {
+                col_n = __ldg(I.colors + nxt + lane);
+                lab_n = I.labels[nxt + lane];
+                if (!kMap) cnt_n = __ldg(I.counts + nxt + lane);
             }
             int p = p0;
             if (p >= K) {                          // invalid input membership
@@ -289,10 +329,8 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
             int mpos = 0;
             int j = 1;
             if (active) {
-                const float4* row = P.tab + (size_t)p * K;
+                const float4* row = tab + (size_t)p * K;
                 bool more = true;
-                // four entries per step; the row is sorted, so when the last
-                // of them is below the bound, all four are visited
                 for (; more && j + 3 < K; j += 4) {
                     const float4 e0 = row[j], e1 = row[j + 1], e2 = row[j + 2], e3 = row[j + 3];
                     if (e3.x < prev) {
@@ -325,10 +363,10 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
                     WSM_VISIT(e, j);
                 }
                 ev += (unsigned long long)j;       // c_p plus the j - 1 visited centers
-                const int lab = mpos ? P.tab_nb[(size_t)p * K + mpos] : p;
-                if (lab != p0) P.labels[i] = (uint8_t)lab;
+                const int lab = mpos ? tab_nb[(size_t)p * K + mpos] : p;
+                if (lab != p0) I.labels[i] = (uint8_t)lab;
                 if (kMap) {
-                    P.lut[col & 0xFFFFFFu] = (uint8_t)lab;
+                    lut[col & 0xFFFFFFu] = (uint8_t)lab;
                 } else {
                     atomicAdd(s_acc + 4 * lab + 0, cnt * ((col >> 16) & 255u));
                     atomicAdd(s_acc + 4 * lab + 1, cnt * ((col >> 8) & 255u));
@@ -341,7 +379,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
                 }
             }
         }
-        if (bad) atomicOr(&P.ctrl->status, ST_BAD_LABEL);
+        if (bad) atomicOr(P.status, ST_BAD_LABEL);
         sse_fx = warp_sum_u64(sse_fx);
         ev = warp_sum_u64(ev);
         npix = warp_sum_u64(npix);
@@ -357,14 +395,14 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
             unsigned long long t = 0;
             for (int w = 0; w < WPB; ++w) t += s_red[tid][w];
             if (kMap) {
-                if (tid == 1 && t) atomicAdd(&P.ctrl->evaluated, t);
+                if (tid == 1 && t) atomicAdd(&ctrl->evaluated, t);
             } else if (t) {
-                atomicAdd(P.sums64 + (size_t)(buf * kCopies + copy) * 4 + tid, t);
+                atomicAdd(sums64 + (size_t)(buf * kCopies + copy) * 4 + tid, t);
             }
         }
         if (kMap) break;
         {
-            unsigned* dst = P.sums + (size_t)(buf * kCopies + copy) * 5 * K;
+            unsigned* dst = sums + (size_t)(buf * kCopies + copy) * s5;
             for (int j = tid; j < 5 * K; j += T) {
                 const unsigned v = s_acc[j];
                 if (v) {
@@ -373,15 +411,15 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
                 }
             }
         }
-        if (!grid_sync(P.ctrl, G)) return;
+        if (!grid_sync(&ctrl->bar_count, P.status, G)) return;
 
         // ---------------- phase A: totals, centers, stop rule, next table ----------------
         {
-            const unsigned* src = P.sums + (size_t)buf * kCopies * 5 * K;
+            const unsigned* src = sums + (size_t)buf * kCopies * s5;
             for (int j = tid; j < 5 * K; j += T) {
                 unsigned v[kCopies];
 #pragma unroll
-                for (int c = 0; c < kCopies; ++c) v[c] = src[(size_t)c * 5 * K + j];
+                for (int c = 0; c < kCopies; ++c) v[c] = src[(size_t)c * s5 + j];
                 unsigned t = 0;
                 if (j < 4 * K) {
 #pragma unroll
@@ -394,7 +432,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
             }
         }
         if (wid == 0) {
-            const unsigned long long* s64 = P.sums64 + (size_t)buf * kCopies * 4;
+            const unsigned long long* s64 = sums64 + (size_t)buf * kCopies * 4;
             unsigned long long fx = 0, evt = 0, N = 0, nz = 0;
             if (lane < kCopies) {
                 fx = s64[lane * 4 + 0];
@@ -420,16 +458,19 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
                 s_stop = stop;
                 if (b == 0) {
                     if (it < kMaxTrace)
-                        P.trace[it] = N ? (double)fx * (1.0 / 1048576.0) / (double)N : 0.0;
-                    P.ctrl->iters_done = done;
-                    P.ctrl->evaluated += evt;
+                        trace[it] = N ? (double)fx * (1.0 / 1048576.0) / (double)N : 0.0;
+                    ctrl->iters_done = done;
+                    ctrl->evaluated += evt;
                 }
             }
         }
-        if (b == 0) {   // clear the accumulators of the next pass (read last two barriers ago)
-            unsigned* nxt = P.sums + (size_t)(buf ^ 1) * kCopies * 5 * K;
-            for (int j = tid; j < kCopies * 5 * K; j += T) nxt[j] = 0u;
-            if (tid < 4 * kCopies) P.sums64[(size_t)(buf ^ 1) * kCopies * 4 + tid] = 0ull;
+        if (b == 0) {   // clear the accumulators of the next pass (read two barriers ago)
+            unsigned* nxt = sums + (size_t)(buf ^ 1) * kCopies * s5;
+            for (int j = tid; j < kCopies * 5 * K; j += T) {
+                const int c = j / (5 * K), r = j - c * 5 * K;
+                nxt[(size_t)c * s5 + r] = 0u;
+            }
+            if (tid < 4 * kCopies) sums64[(size_t)(buf ^ 1) * kCopies * 4 + tid] = 0ull;
         }
         __syncthreads();
         {
@@ -442,7 +483,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
                                       : s_cf[4 * k + ch];
             }
             if (b == 0)
-                for (int j = tid; j < 4 * K; j += T) P.acc[j] = s_acc[j];
+                for (int j = tid; j < 4 * K; j += T) acc[j] = s_acc[j];
         }
         __syncthreads();
         // Row bound for the next pass: a member x of cluster k had
@@ -459,24 +500,33 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(SortMeansParams P
         }
         __syncthreads();
         if (s_stop) break;
-        build_rows(P, s_c, s_thr, s_key, s_rank, s_cnt);
-        if (!grid_sync(P.ctrl, G)) return;
+        build_rows(K, G, b, s_c, s_thr, s_wkey, tab, tab_nb);
+        if (!grid_sync(&ctrl->bar_count, P.status, G)) return;
     }
 
     // centers after the last update
     if (!kMap && b == 0)
-        for (int k = tid; k < K; k += T) P.centers[k] = s_c[k];
+        for (int k = tid; k < K; k += T) I.centers[k] = s_c[k];
 }
 #undef WSM_VISIT
 
-static size_t sortmeans_smem(int K) { return (size_t)K * (16 + 16 + 8 + 20 + 4 + 4); }
+// Dynamic shared memory of k_sortmeans for palettes of up to KM colors.
+static size_t sortmeans_smem(int KM) {
+    return (size_t)KM * (16 + 16 + 20 + 4) + (size_t)(kIterThreads / 32) * KM * 8;
+}
 
 // Co-residency of the persistent kernel: blocks per SM for the largest K.
 int iterate_kernel_setup(wsm_handle* h) {
     int occ_it = 0, occ_map = 0;
-    size_t smem = sortmeans_smem(h->max_K);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ_it, k_sortmeans<false>, kIterThreads, smem);
+    const size_t smem = sortmeans_smem(h->max_K);
+    cudaError_t e = cudaFuncSetAttribute(k_sortmeans<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sortmeans<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_it, k_sortmeans<false>,
+                                                          kIterThreads, smem);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_map, k_sortmeans<true>,
                                                           kIterThreads, smem);
@@ -488,50 +538,150 @@ int iterate_kernel_setup(wsm_handle* h) {
     return WSM_OK;
 }
 
-// Blocks for n colors: enough for every thread to hold at least one color,
-// at most `cap` (the co-resident grid).
-static int sortmeans_grid(int cap, int64_t n) {
-    int64_t want = (n + kIterThreads - 1) / kIterThreads;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
+// Blocks of one image's group: enough for every lane to hold a color and for
+// every warp to hold a table row, within the available blocks.
+static int64_t group_want(int64_t n, int K) {
+    const int64_t for_colors = (n + kIterThreads - 1) / kIterThreads;
+    const int64_t for_rows = (K + kIterThreads / 32 - 1) / (kIterThreads / 32);
+    return std::max<int64_t>(1, std::max(for_colors, for_rows));
 }
 
-static int launch_with(bool map_mode, const uint32_t* colors, const uint32_t* counts, int64_t n,
-                       int K, float* centers, uint8_t* labels, int max_iter, double eps,
-                       float4* tab, uint8_t* tab_nb, unsigned* sums,
-                       unsigned long long* sums64, unsigned long long* acc, double* trace,
-                       uint8_t* lut, Ctrl* ctrl, int grid, cudaStream_t s) {
-    SortMeansParams P;
-    P.colors = colors;
-    P.counts = counts;
-    P.n = n;
-    P.K = K;
-    P.centers = reinterpret_cast<float4*>(centers);
-    P.labels = labels;
+// Split `grid` co-resident blocks into one group per image, proportional to
+// each image's need (at least one block each); returns the total used.
+static int split_groups(const ItemDesc* items, int n_items, int grid, int* first_blk) {
+    std::vector<int64_t> want(n_items);
+    int64_t total = 0;
+    for (int i = 0; i < n_items; ++i) {
+        want[i] = group_want(items[i].n, items[i].K);
+        total += want[i];
+    }
+    std::vector<int> g(n_items, 1);
+    if (total <= grid) {
+        for (int i = 0; i < n_items; ++i) g[i] = (int)want[i];
+    } else {
+        int left = grid - n_items;
+        std::vector<std::pair<double, int>> frac;
+        for (int i = 0; i < n_items; ++i) {
+            const double share = (double)left * (double)(want[i] - 1) / (double)(total - n_items);
+            const int add = (int)share;
+            g[i] += add;
+            frac.push_back({share - add, i});
+        }
+        int used = 0;
+        for (int i = 0; i < n_items; ++i) used += g[i];
+        std::sort(frac.begin(), frac.end(), [](auto& a, auto& c) { return a.first > c.first; });
+        for (size_t q = 0; q < frac.size() && used < grid; ++q, ++used) g[frac[q].second] += 1;
+    }
+    first_blk[0] = 0;
+    for (int i = 0; i < n_items; ++i) first_blk[i + 1] = first_blk[i] + g[i];
+    return first_blk[n_items];
+}
+
+static Scratch handle_scratch(wsm_handle* h) {
+    Scratch sc;
+    sc.tab = h->tab;
+    sc.tab_nb = h->tab_nb;
+    sc.sums = h->sums;
+    sc.sums64 = h->sums64;
+    sc.acc = h->acc;
+    sc.trace = h->trace;
+    sc.lut = h->lut;
+    sc.ctrl = h->slot_ctrl;
+    sc.max_K = h->max_K;
+    return sc;
+}
+
+// One cooperative launch over n_items <= kMaxBatch images (item i in slot
+// i, or in the slots given).  grid_cap limits the blocks used.
+int launch_batch(const Scratch& sc, unsigned* status, bool map_mode, const ItemDesc* items,
+                 int n_items, int max_iter, double eps, int grid_cap, cudaStream_t s) {
+    BatchParams P;
+    P.sc = sc;
+    P.status = status;
+    P.n_items = n_items;
     P.max_iter = max_iter;
     P.eps = eps;
-    P.tab = tab;
-    P.tab_nb = tab_nb;
-    P.sums = sums;
-    P.sums64 = sums64;
-    P.acc = acc;
-    P.trace = trace;
-    P.lut = lut;
-    P.ctrl = ctrl;
+    int KM = 1;
+    for (int i = 0; i < n_items; ++i) {
+        P.item[i] = items[i];
+        KM = std::max(KM, items[i].K);
+    }
+    const int grid = split_groups(items, n_items, grid_cap, P.first_blk);
     void* args[] = {&P};
     void* fn = map_mode ? (void*)k_sortmeans<true> : (void*)k_sortmeans<false>;
-    cudaError_t e = cudaMemsetAsync(ctrl, 0, kLaunchResetBytes, s);
+    // Clear the barrier counters and the accumulators of the slots used.  The
+    // items of a launch use consecutive slots, so one memset per array does.
+    int lo = items[0].slot, hi = items[0].slot;
+    for (int i = 1; i < n_items; ++i) {
+        lo = std::min(lo, items[i].slot);
+        hi = std::max(hi, items[i].slot);
+    }
+    const size_t nsl = (size_t)(hi - lo + 1), s5 = (size_t)5 * sc.max_K;
+    cudaError_t e = cudaMemsetAsync(sc.ctrl + lo, 0, sizeof(Ctrl) * nsl, s);
     if (e == cudaSuccess)
-        e = cudaLaunchCooperativeKernel(fn, grid, kIterThreads, args, sortmeans_smem(K), s);
+        e = cudaMemsetAsync(sc.sums + (size_t)lo * 2 * kCopies * s5, 0,
+                            sizeof(unsigned) * 2 * kCopies * s5 * nsl, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(sc.sums64 + (size_t)lo * 2 * kCopies * 4, 0,
+                            sizeof(unsigned long long) * 2 * kCopies * 4 * nsl, s);
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel(fn, grid, kIterThreads, args, sortmeans_smem(sc.max_K), s);
     if (e != cudaSuccess) return cuda_fail(e, "sort-means launch");
+    (void)KM;
     return WSM_OK;
 }
 
 int launch_sortmeans(wsm_handle* h, bool map_mode, const uint32_t* colors, const uint32_t* counts,
                      int64_t n, int K, float* centers, uint8_t* labels, int max_iter, double eps,
                      cudaStream_t s) {
-    return launch_with(map_mode, colors, counts, n, K, centers, labels, max_iter, eps,
-                       h->tab, h->tab_nb, h->sums, h->sums64,
-                       h->acc, h->trace, h->lut, h->ctrl, sortmeans_grid(h->iter_grid, n), s);
+    ItemDesc it;
+    it.colors = colors;
+    it.counts = counts;
+    it.labels = labels;
+    it.centers = reinterpret_cast<float4*>(centers);
+    it.n = n;
+    it.K = K;
+    it.slot = 0;
+    return launch_batch(handle_scratch(h), &h->ctrl->status, map_mode, &it, 1, max_iter, eps,
+                        h->iter_grid, s);
+}
+
+// The final assignment of n_items images (slots slot0, slot0 + 1, ...) in
+// one persistent launch in map mode.
+int launch_map_items(wsm_handle* h, const wsm_item* items, int n_items, int slot0,
+                     cudaStream_t s) {
+    ItemDesc d[kMaxBatch];
+    for (int q = 0; q < n_items; ++q) {
+        d[q].colors = items[q].d_colors;
+        d[q].counts = nullptr;
+        d[q].labels = items[q].d_labels;
+        d[q].centers = reinterpret_cast<float4*>(items[q].d_centers);
+        d[q].n = items[q].n_unique;
+        d[q].K = items[q].K;
+        d[q].slot = slot0 + q;
+    }
+    return launch_batch(handle_scratch(h), &h->ctrl->status, true, d, n_items, 1, 0.0,
+                        h->iter_grid, s);
+}
+
+// Checks of one batch item shared by the iterate and map entry points.
+int check_item(wsm_handle* h, const wsm_item& it, bool need_pixels, bool need_counts) {
+    if (it.K < 1 || it.K > h->max_K) return fail(WSM_E_INVAL, "K out of [1, max_K]");
+    if (it.n_unique < 1 || it.n_unique > h->max_unique)
+        return fail(WSM_E_INVAL, "n_unique must be in [1, max_unique]");
+    if (!it.d_colors || !it.d_centers || !it.d_labels || (need_counts && !it.d_counts))
+        return fail(WSM_E_INVAL, "null device pointer");
+    if ((uintptr_t)it.d_centers & 15) return fail(WSM_E_INVAL, "centers must be 16-byte aligned");
+    if (need_pixels) {
+        if (it.pixel_stride != 3 && it.pixel_stride != 4)
+            return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
+        if (it.n_pixels < 1 || it.n_pixels > h->max_pixels || it.n_unique > it.n_pixels)
+            return fail(WSM_E_INVAL, "n_pixels must be in [max(1, n_unique), max_pixels]");
+        if (!it.d_rgb || !it.d_index) return fail(WSM_E_INVAL, "null pixel or index pointer");
+        if (it.pixel_stride == 4 && ((uintptr_t)it.d_rgb & 3))
+            return fail(WSM_E_INVAL, "4-byte pixels must be 4-byte aligned");
+    }
+    return WSM_OK;
 }
 
 }  // namespace wsm
@@ -557,7 +707,7 @@ extern "C" int wsm_iterate(wsm_handle* h, const uint32_t* d_colors, const uint32
                           max_iter, eps, s);
     if (rc != WSM_OK) return rc;
     if (iters_done || sse_trace) {
-        cudaError_t e = cudaMemcpyAsync(&h->host_ctrl->iters_done, &h->ctrl->iters_done,
+        cudaError_t e = cudaMemcpyAsync(&h->host_ctrl->iters_done, &h->slot_ctrl[0].iters_done,
                                         sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(e, "iteration count copy");
         rc = read_status(h, s);
@@ -573,6 +723,49 @@ extern "C" int wsm_iterate(wsm_handle* h, const uint32_t* d_colors, const uint32
     return WSM_OK;
 }
 
+extern "C" int wsm_iterate_batch(wsm_handle* h, const wsm_item* items, int n_items, int max_iter,
+                                 double eps, int* iters_done, wsm_stream stream) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (n_items < 0 || (n_items > 0 && !items)) return fail(WSM_E_INVAL, "bad item list");
+    if (n_items > h->slots)
+        return fail(WSM_E_INVAL, "more items than reserved slots (wsm_reserve_batch)");
+    if (max_iter < 0 || max_iter > kMaxTrace)
+        return fail(WSM_E_INVAL, "max_iter must be in [0, 4096]");
+    for (int i = 0; i < n_items; ++i) {
+        rc = check_item(h, items[i], false, true);
+        if (rc != WSM_OK) return rc;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
+        const int m = std::min(kMaxBatch, n_items - i0);
+        ItemDesc d[kMaxBatch];
+        for (int q = 0; q < m; ++q) {
+            const wsm_item& it = items[i0 + q];
+            d[q].colors = it.d_colors;
+            d[q].counts = it.d_counts;
+            d[q].labels = it.d_labels;
+            d[q].centers = reinterpret_cast<float4*>(it.d_centers);
+            d[q].n = it.n_unique;
+            d[q].K = it.K;
+            d[q].slot = i0 + q;
+        }
+        rc = launch_batch(handle_scratch(h), &h->ctrl->status, false, d, m, max_iter, eps,
+                          h->iter_grid, s);
+        if (rc != WSM_OK) return rc;
+    }
+    if (iters_done && n_items > 0) {
+        rc = read_status(h, s);
+        if (rc != WSM_OK) return rc;
+        for (int i = 0; i < n_items; ++i) {
+            cudaError_t e = cudaMemcpy(&iters_done[i], &h->slot_ctrl[i].iters_done, sizeof(int),
+                                       cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e, "iteration count copy");
+        }
+    }
+    return WSM_OK;
+}
+
 extern "C" int wsm_iterate_stats(wsm_handle* h, int K, int64_t* evaluated, int64_t* S, int64_t* W,
                                  wsm_stream stream) {
     int rc = check_handle(h);
@@ -582,7 +775,7 @@ extern "C" int wsm_iterate_stats(wsm_handle* h, int K, int64_t* evaluated, int64
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "stream sync");
     Ctrl c;
-    e = cudaMemcpy(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(&c, &h->slot_ctrl[0], sizeof(Ctrl), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "stats copy");
     if (evaluated) *evaluated = (int64_t)c.evaluated;
     if (S || W) {
@@ -647,6 +840,9 @@ static int static_setup(int dev, StaticSetup** out) {
         int sms = 0, occ = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sortmeans<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sortmeans_smem(kStaticMaxK));
+        if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &occ, k_sortmeans<false>, kIterThreads, sortmeans_smem(kStaticMaxK));
         if (e != cudaSuccess) return cuda_fail(e, "static set-up query");
@@ -688,12 +884,25 @@ extern "C" int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_c
     // the status word starts at zero on every call (the launch clears the rest)
     e = cudaMemsetAsync(&ctrl->status, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return cuda_fail(e, "wsm_iterate_noalloc status clear");
-    rc = launch_with(false, d_colors, d_counts, n_unique, K, d_centers, d_labels, max_iter, eps,
-                     reinterpret_cast<float4*>(base), base + kStaticOffNb,
-                     reinterpret_cast<unsigned*>(base + kStaticOffSums),
-                     reinterpret_cast<unsigned long long*>(base + kStaticOffSums64),
-                     reinterpret_cast<unsigned long long*>(base + kStaticOffAcc), trace, nullptr,
-                     ctrl, sortmeans_grid(st->grid, n_unique), s);
+    Scratch sc;
+    sc.tab = reinterpret_cast<float4*>(base);
+    sc.tab_nb = base + kStaticOffNb;
+    sc.sums = reinterpret_cast<unsigned*>(base + kStaticOffSums);
+    sc.sums64 = reinterpret_cast<unsigned long long*>(base + kStaticOffSums64);
+    sc.acc = reinterpret_cast<unsigned long long*>(base + kStaticOffAcc);
+    sc.trace = trace;
+    sc.lut = nullptr;
+    sc.ctrl = ctrl;
+    sc.max_K = kStaticMaxK;
+    ItemDesc it;
+    it.colors = d_colors;
+    it.counts = d_counts;
+    it.labels = d_labels;
+    it.centers = reinterpret_cast<float4*>(d_centers);
+    it.n = n_unique;
+    it.K = K;
+    it.slot = 0;
+    rc = launch_batch(sc, &ctrl->status, false, &it, 1, max_iter, eps, st->grid, s);
     if (rc != WSM_OK) return rc;
     if (iters_done || sse_trace) {
         Ctrl host;

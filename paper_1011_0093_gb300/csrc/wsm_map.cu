@@ -15,6 +15,8 @@ namespace wsm {
 int launch_sortmeans(wsm_handle* h, bool map_mode, const uint32_t* colors, const uint32_t* counts,
                      int64_t n, int K, float* centers, uint8_t* labels, int max_iter, double eps,
                      cudaStream_t s);
+int check_item(wsm_handle* h, const wsm_item& it, bool need_pixels, bool need_counts);
+int launch_map_items(wsm_handle* h, const wsm_item* items, int n_items, int slot0, cudaStream_t s);
 
 __device__ __forceinline__ uint32_t key_of(const uint8_t* __restrict__ rgb, int64_t p, int stride) {
     if (stride == 4) {
@@ -31,6 +33,30 @@ __global__ void __launch_bounds__(256) k_gather(const uint8_t* __restrict__ rgb,
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x)
         index[p] = lut[key_of(rgb, p, stride)];
+}
+
+// The gather of a batch: image i owns blocks [first_blk[i], first_blk[i+1])
+// and reads the color->label table of its slot.
+struct GatherBatch {
+    int n_items;
+    int first_blk[kMaxBatch + 1];
+    const uint8_t* rgb[kMaxBatch];
+    uint8_t* index[kMaxBatch];
+    int64_t n[kMaxBatch];
+    int stride[kMaxBatch];
+    int slot[kMaxBatch];
+    const uint8_t* lut;        // slot s at lut + s * 2^24
+};
+
+__global__ void __launch_bounds__(256) k_gather_batch(const __grid_constant__ GatherBatch B) {
+    int i = 0;
+    while (i + 1 < B.n_items && (int)blockIdx.x >= B.first_blk[i + 1]) ++i;
+    const int g0 = B.first_blk[i], G = B.first_blk[i + 1] - g0;
+    const uint8_t* lut = B.lut + (size_t)B.slot[i] * kHistBins;
+    const int64_t n = B.n[i];
+    for (int64_t p = (int64_t)(blockIdx.x - g0) * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)G * blockDim.x)
+        B.index[i][p] = lut[key_of(B.rgb[i], p, B.stride[i])];
 }
 
 constexpr int kMseThreads = 256;
@@ -127,6 +153,47 @@ extern "C" int wsm_map(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, in
     k_gather<<<grid, 256, 0, s>>>(d_rgb, n_pixels, pixel_stride, h->lut, d_index);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "gather launch");
+    return WSM_OK;
+}
+
+extern "C" int wsm_map_batch(wsm_handle* h, const wsm_item* items, int n_items,
+                             wsm_stream stream) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (n_items < 0 || (n_items > 0 && !items)) return fail(WSM_E_INVAL, "bad item list");
+    if (n_items > h->slots)
+        return fail(WSM_E_INVAL, "more items than reserved slots (wsm_reserve_batch)");
+    for (int i = 0; i < n_items; ++i) {
+        rc = check_item(h, items[i], true, false);
+        if (rc != WSM_OK) return rc;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
+        const int m = std::min(kMaxBatch, n_items - i0);
+        rc = launch_map_items(h, items + i0, m, i0, s);
+        if (rc != WSM_OK) return rc;
+        GatherBatch B;
+        B.n_items = m;
+        B.lut = h->lut;
+        int64_t total = 0;
+        for (int q = 0; q < m; ++q) total += items[i0 + q].n_pixels;
+        const int64_t budget = (int64_t)h->sms * 16;
+        B.first_blk[0] = 0;
+        for (int q = 0; q < m; ++q) {
+            const wsm_item& it = items[i0 + q];
+            B.rgb[q] = it.d_rgb;
+            B.index[q] = it.d_index;
+            B.n[q] = it.n_pixels;
+            B.stride[q] = it.pixel_stride;
+            B.slot[q] = i0 + q;
+            const int64_t want = (it.n_pixels + 255) / 256;
+            const int64_t share = std::max<int64_t>(1, budget * it.n_pixels / std::max<int64_t>(total, 1));
+            B.first_blk[q + 1] = B.first_blk[q] + (int)std::min(want, share);
+        }
+        k_gather_batch<<<B.first_blk[m], 256, 0, s>>>(B);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "gather launch");
+    }
     return WSM_OK;
 }
 

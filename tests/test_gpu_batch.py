@@ -1,0 +1,109 @@
+"""The batched persistent launch (wsm_iterate_batch, wsm_map_batch) gives, for
+every image of a batch, exactly what the single-image calls give: the same
+centers, memberships, iteration counts and index images, bit for bit (the
+per-image computation is identical and every reduction is exact), for images
+of uneven sizes, palettes and convergence lengths."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wsm():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1011_0093_gb300 import build as B
+    B.build()
+    import paper_1011_0093_gb300 as w
+    return w
+
+
+def prepare(wsm, h, img, K, seed):
+    n = img.shape[0] * img.shape[1]
+    rgb = torch.from_numpy(np.ascontiguousarray(img)).cuda()
+    colors = torch.empty(n, dtype=torch.uint32, device="cuda")
+    counts = torch.empty(n, dtype=torch.uint32, device="cuda")
+    nu = wsm.wsm_reduce(h, rgb, colors, counts)
+    colors, counts = colors[:nu], counts[:nu]
+    centers = torch.empty((K, 4), dtype=torch.float32, device="cuda")
+    labels = torch.empty(nu, dtype=torch.uint8, device="cuda")
+    wsm.wsm_init(h, colors, nu, K, seed, centers, labels)
+    index = torch.empty(img.shape[:2], dtype=torch.uint8, device="cuda")
+    return dict(rgb=rgb, colors=colors, counts=counts, n_unique=nu, K=K, centers=centers,
+                labels=labels, index=index)
+
+
+def clone(im):
+    out = dict(im)
+    for k in ("centers", "labels", "index"):
+        out[k] = im[k].clone()
+    return out
+
+
+BATCH = [((512, 512), 7, 24, 256), ((256, 256), 0, 6, 16), ((96, 80), 5, 6, 16),
+         ((300, 211), 8, 9, 64), ((512, 512), 2, 7, 128), ((64, 64), 2, 6, 8),
+         ((700, 300), 11, 15, 32), ((40, 37), 50, 0, 5)]
+
+
+@pytest.mark.parametrize("max_iter,eps", [(10, 0.0), (100, 1e-4)])
+def test_batch_equals_single_calls(wsm, max_iter, eps):
+    imgs = [synth.image(hw[0], hw[1], seed, noise) if noise else synth.tiny(hw[0], hw[1], seed, 4)
+            for hw, seed, noise, _ in BATCH]
+    with wsm.Handle(256, 512 * 512) as h:
+        wsm.wsm_reserve_batch(h, len(BATCH))
+        items = [prepare(wsm, h, img, K, 100 + q) for q, (img, (_, _, _, K)) in
+                 enumerate(zip(imgs, BATCH))]
+        single = [clone(im) for im in items]
+        iters_single = []
+        for im in single:
+            done, _ = wsm.wsm_iterate(h, im["colors"], im["counts"], im["n_unique"], im["K"],
+                                      im["centers"], im["labels"], max_iter, eps)
+            iters_single.append(done)
+            wsm.wsm_map(h, im["rgb"], im["colors"], im["n_unique"], im["centers"], im["K"],
+                        im["labels"], im["index"])
+        batch = [clone(im) for im in items]
+        iters_batch = wsm.wsm_iterate_batch(h, batch, max_iter, eps)
+        wsm.wsm_map_batch(h, batch)
+        wsm.wsm_sync_status(h)
+    assert iters_batch == iters_single
+    if eps > 0:
+        assert len(set(iters_single)) > 1          # uneven convergence lengths in one launch
+    for a, b in zip(single, batch):
+        assert torch.equal(a["centers"], b["centers"])
+        assert torch.equal(a["labels"], b["labels"])
+        assert torch.equal(a["index"], b["index"])
+
+
+def test_batch_matches_oracle_and_more_than_one_launch(wsm):
+    """A batch of 50 small images spans two launches (48 per launch); each
+    image's index image matches the oracle's wherever no near-tie decides."""
+    specs = [(48 + (q % 7) * 8, 40 + (q % 5) * 8, 200 + q, q % 9, 4 + (q % 13)) for q in range(50)]
+    imgs = [synth.image(hh, ww, seed, noise) for hh, ww, seed, noise, _ in specs]
+    with wsm.Handle(64, 112 * 72) as h:
+        wsm.wsm_reserve_batch(h, len(specs))
+        items = [prepare(wsm, h, img, K, 7 + q) for q, (img, (*_, K)) in
+                 enumerate(zip(imgs, specs))]
+        iters = wsm.wsm_iterate_batch(h, items, 10, 0.0)
+        wsm.wsm_map_batch(h, items)
+        wsm.wsm_sync_status(h)
+    assert iters == [10] * len(specs)
+    for img, im, (*_, K), q in zip(imgs, items, specs, range(len(specs))):
+        ref = oracle.quantize(img, K, 7 + q, 10, 0.0)
+        gc = im["centers"].cpu().numpy()[:, :3]
+        best, second, _ = oracle.exhaustive(ref["colors"], ref["centers"])
+        if np.all(second - best > 1e-3):
+            assert np.abs(gc - ref["centers"]).max() <= 1e-4
+            assert np.array_equal(im["index"].cpu().numpy().ravel(), ref["index"])
+
+
+def test_batch_rejects_more_items_than_slots(wsm):
+    img = synth.image(32, 32, 1, 3)
+    with wsm.Handle(16, 32 * 32) as h:
+        items = [prepare(wsm, h, img, 4, q) for q in range(2)]
+        with pytest.raises(wsm.WsmError, match="slots"):
+            wsm.wsm_iterate_batch(h, items, 5, 0.0)
