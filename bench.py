@@ -44,10 +44,10 @@ H = W = 512
 METRIC = "unique-color assignments/s per iter (K=256) vs FP32 peak; 512² images/s end-to-end"
 UNIT = "assignments/s"
 L2_FLUSH_BYTES = 256 << 20
-# per image: hist24, scan_count, scan_emit, init, mse_partial, mse_final; per step:
-# the batched sort-means launch, the batched map launch and the batched gather
-KERNELS_PER_IMAGE = 6
-KERNELS_PER_STEP = 3
+# per step, all images together: hist24, scan_count, scan_emit (up to 16 images
+# per launch), init, the sort-means launch, the map-mode sort-means launch, the
+# gather, mse_partial and mse_final (up to 48 images per launch)
+KERNELS_PER_STEP = 9
 
 
 def workload(rank: int):
@@ -209,20 +209,17 @@ def run_gpu(args):
     mse = torch.empty(len(images), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     it_events = []          # (tag, start, end) around every batched iterate launch
-    n_unique = [0] * len(images)
+    seeds = [image_seed(rank, s) for s in range(len(images))]
+    items = [dict(rgb=d_imgs[s], colors=colors[s], counts=counts[s], K=K_PALETTE,
+                  centers=centers[s], labels=labels[s], index=index[s])
+             for s in range(len(images))]
 
     def step(record: bool):
-        # a1, a2 per image; a3-a6 for all images in one persistent launch;
-        # a7 for all images in one persistent launch + one gather; a8 per image
-        items = []
-        for s, img in enumerate(d_imgs):
-            nu = wsm.wsm_reduce(handle, img, colors[s], counts[s])
-            n_unique[s] = nu
-            wsm.wsm_init(handle, colors[s], nu, K_PALETTE, image_seed(rank, s), centers[s],
-                         labels[s])
-            items.append(dict(rgb=img, colors=colors[s], counts=counts[s], n_unique=nu,
-                              K=K_PALETTE, centers=centers[s], labels=labels[s],
-                              index=index[s]))
+        # every step of the path is one batched call over all images:
+        # a1 (one host sync for all N'), a2, a3-a6 (one persistent launch),
+        # a7 (one persistent launch + one gather), a8
+        wsm.wsm_reduce_batch(handle, items)
+        wsm.wsm_init_batch(handle, items, seeds)
         if record:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -232,9 +229,7 @@ def run_gpu(args):
             e1.record(stream)
             it_events.append((-1, e0, e1))
         wsm.wsm_map_batch(handle, items)
-        for s, img in enumerate(d_imgs):
-            wsm.wsm_distortion(handle, img, centers[s], K_PALETTE, index[s], d_mse=mse[s:s + 1],
-                               sync=False)
+        wsm.wsm_distortion_batch(handle, items, d_mse=mse, sync=False)
 
     # distances evaluated per image (deterministic: same inputs every step)
     evaluated = []
@@ -268,7 +263,7 @@ def run_gpu(args):
         step_ms.append(a.elapsed_time(b))
     barrier()
     wsm.wsm_sync_status(handle)
-    units_step = sum(n_unique) * ITERS
+    units_step = sum(im["n_unique"] for im in items) * ITERS
     total_ms = sum(step_ms)
 
     # e2e through the public API from pinned host memory
@@ -281,11 +276,12 @@ def run_gpu(args):
 
     def e2e_step():
         imgs = [himg.to(dev, non_blocking=True) for himg in h_imgs]
-        qs = wsm.quantize_batch(imgs, K_PALETTE, [image_seed(rank, s) for s in range(len(imgs))],
-                                max_iter=ITERS, eps=0.0, handle=handle, mse=False)
-        for s, (img, q) in enumerate(zip(imgs, qs)):
-            wsm.wsm_distortion(handle, img, q.centers, K_PALETTE, q.index, d_mse=mse[s:s + 1],
-                               sync=False)
+        qs = wsm.quantize_batch(imgs, K_PALETTE, seeds, max_iter=ITERS, eps=0.0, handle=handle,
+                                mse=False)
+        wsm.wsm_distortion_batch(handle, [dict(rgb=img, K=K_PALETTE, centers=q.centers,
+                                               index=q.index) for img, q in zip(imgs, qs)],
+                                 d_mse=mse, sync=False)
+        for s, q in enumerate(qs):
             out_idx[s].copy_(q.index, non_blocking=True)
             out_pal[s].copy_(q.centers, non_blocking=True)
         out_mse.copy_(mse, non_blocking=True)
@@ -338,7 +334,8 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "sweep 8x512x512 noise 0..24 per GPU, K=256, WSM 10 iterations",
-                       "unique_colors": n_unique, "images_per_step": len(images) * world,
+                       "unique_colors": [im["n_unique"] for im in items],
+                       "images_per_step": len(images) * world,
                        "images_per_s": len(images) * world * args.steps / (total_ms * 1e-3),
                        "images_per_s_e2e": len(images) * world * args.steps / (e2e_total * 1e-3),
                        "l2": "flushed between steps (256 MiB write)",
@@ -354,7 +351,7 @@ def run_gpu(args):
                          "flop_per_launch": sum(it_flop) / len(it_flop)},
             "cpu_baseline": cpu,
             "clocks": clk,
-            "gpu_launches": (KERNELS_PER_IMAGE * len(images) + KERNELS_PER_STEP) * args.steps,
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
         }
         print(json.dumps(line), flush=True)
     handle.close()

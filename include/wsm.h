@@ -163,9 +163,15 @@ WSM_API int wsm_iterate(wsm_handle* h, const uint32_t* d_colors, const uint32_t*
 WSM_API int wsm_iterate_stats(wsm_handle* h, int K, int64_t* evaluated, int64_t* S, int64_t* W,
                       wsm_stream stream);
 
-/* One image of a batch call (wsm_iterate_batch, wsm_map_batch); fields as for
- * the single-image calls.  d_rgb, n_pixels, pixel_stride and d_index are
- * used by wsm_map_batch only, d_counts by wsm_iterate_batch only. */
+/* One image of a batch call; fields as for the single-image calls.  Which
+ * fields each batch call reads (r) or writes (w):
+ *   wsm_reduce_batch      d_rgb n_pixels pixel_stride (r); d_colors d_counts
+ *                         (w, device memory of n_pixels entries each, written
+ *                         through the const pointers); n_unique (w, host)
+ *   wsm_init_batch        K d_colors n_unique (r); d_centers d_labels (w)
+ *   wsm_iterate_batch     K d_colors d_counts n_unique (r); d_centers d_labels (rw)
+ *   wsm_map_batch         every field but d_counts (r); d_labels d_index (w)
+ *   wsm_distortion_batch  d_rgb n_pixels pixel_stride K d_centers d_index (r) */
 typedef struct {
     const uint8_t* d_rgb;       /* [n_pixels][pixel_stride] */
     int64_t n_pixels;
@@ -180,8 +186,10 @@ typedef struct {
 } wsm_item;
 
 /* Reserve per-image scratch for batches of up to max_items images (about
- * 17.2 MiB each at max_K = 256, dominated by the color->label table).
- * Synchronises the device.  A new handle has one slot.
+ * 17.2 MiB each at max_K = 256, dominated by the color->label table), plus
+ * the unique-color reduction scratch of min(max_items, 16) images (66 MiB
+ * each: the 2^24-bin histogram and its occupancy map).  Synchronises the
+ * device.  A new handle has one slot.
  * Errors: WSM_E_INVAL, WSM_E_NOMEM (the handle keeps one slot). */
 WSM_API int wsm_reserve_batch(wsm_handle* h, int max_items);
 
@@ -197,6 +205,35 @@ WSM_API int wsm_reserve_batch(wsm_handle* h, int max_items);
  * WSM_E_TIMEOUT. */
 WSM_API int wsm_iterate_batch(wsm_handle* h, const wsm_item* items, int n_items, int max_iter,
                               double eps, int* iters_done, wsm_stream stream);
+
+/* Sec. 2, unique colors and their counts for n_items images, as wsm_reduce
+ * gives them one by one (same output), in one launch of each reduction
+ * kernel per 16 images and one device synchronisation for the whole batch.
+ * On success items[i].n_unique holds N' of image i; its d_colors and
+ * d_counts hold N' entries (ascending colors) and must have room for
+ * n_pixels.  1 <= n_pixels <= max_pixels.
+ * Errors: WSM_E_INVAL (sizes, pointers, more items than reserved slots). */
+WSM_API int wsm_reduce_batch(wsm_handle* h, wsm_item* items, int n_items, wsm_stream stream);
+
+/* Algorithm 2, first step, for n_items images, as wsm_init would do them
+ * one by one with seeds[i] (same centers and labels): the host draws every
+ * image's K indices (Floyd sampling of splitmix64 draws), one copy moves
+ * them to the device and one launch per 48 images gathers the centers and
+ * zeroes the labels.  seeds: host uint64 [n_items].  Waits, on the host,
+ * only for the previous call's index copy.
+ * Errors: WSM_E_INVAL (K, n_unique < K, pointers, more items than slots). */
+WSM_API int wsm_init_batch(wsm_handle* h, const wsm_item* items, int n_items,
+                           const uint64_t* seeds, wsm_stream stream);
+
+/* Eq. 2 for n_items images, as wsm_distortion gives them one by one (same
+ * values: the sum is exact in 2^-20 units whatever the block split), in one
+ * pair of launches per 48 images.
+ *   d_mse  device double [n_items] (may be NULL)
+ *   mse    host double [n_items] (may be NULL; if given, synchronises and
+ *          reports a palette index >= K as WSM_E_INVAL)
+ * Errors: WSM_E_INVAL (sizes, pointers, more items than reserved slots). */
+WSM_API int wsm_distortion_batch(wsm_handle* h, const wsm_item* items, int n_items,
+                                 double* d_mse, double* mse, wsm_stream stream);
 
 /* Sec. 1, pixel mapping for n_items images: one final pruned assignment per
  * image in one persistent launch (as wsm_map), then one gather launch over

@@ -7,12 +7,15 @@ thin Python layer above it: ``_native`` marshals arguments to the C entry
 points, ``quantize`` chains them for one image.  PyTorch only provides device
 memory and streams.
 """
-from ._native import (MAX_K, MAX_PIXELS, Handle, WsmError, lib, wsm_distortion, wsm_init,
-                      wsm_iterate, wsm_iterate_batch, wsm_iterate_noalloc, wsm_iterate_stats,
-                      wsm_map, wsm_map_batch, wsm_reduce, wsm_reserve_batch, wsm_sync_status)
+from ._native import (MAX_K, MAX_PIXELS, Handle, WsmError, lib, wsm_distortion,
+                      wsm_distortion_batch, wsm_init, wsm_init_batch, wsm_iterate,
+                      wsm_iterate_batch, wsm_iterate_noalloc, wsm_iterate_stats, wsm_map,
+                      wsm_map_batch, wsm_reduce, wsm_reduce_batch, wsm_reserve_batch,
+                      wsm_sync_status)
 from .quantize import Quantized, quantize, quantize_batch
 
 __all__ = ["MAX_K", "MAX_PIXELS", "Handle", "WsmError", "lib", "wsm_reduce", "wsm_init",
            "wsm_iterate", "wsm_iterate_noalloc", "wsm_iterate_stats", "wsm_iterate_batch",
-           "wsm_map_batch", "wsm_reserve_batch", "wsm_map", "wsm_distortion", "wsm_sync_status",
+           "wsm_map_batch", "wsm_reserve_batch", "wsm_reduce_batch", "wsm_init_batch",
+           "wsm_distortion_batch", "wsm_map", "wsm_distortion", "wsm_sync_status",
            "Quantized", "quantize", "quantize_batch"]

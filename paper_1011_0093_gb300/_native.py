@@ -52,6 +52,9 @@ SIGNATURES = {
     "wsm_reserve_batch": (C.c_int, [_P, C.c_int]),
     "wsm_iterate_batch": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_double, _P, _P]),
     "wsm_map_batch": (C.c_int, [_P, _P, C.c_int, _P]),
+    "wsm_reduce_batch": (C.c_int, [_P, _P, C.c_int, _P]),
+    "wsm_init_batch": (C.c_int, [_P, _P, C.c_int, _P, _P]),
+    "wsm_distortion_batch": (C.c_int, [_P, _P, C.c_int, _P, _P, _P]),
     "wsm_distortion": (C.c_int, [_P, _P, _I64, C.c_int, _P, C.c_int, _P, _P,
                                  C.POINTER(C.c_double), _P]),
 }
@@ -270,6 +273,67 @@ def wsm_iterate_batch(h: Handle, images: list[dict], max_iter: int, eps: float,
 def wsm_map_batch(h: Handle, images: list[dict], stream=None):
     arr = _items(images, True, False)
     _check(lib().wsm_map_batch(h.ptr, C.cast(arr, C.c_void_p), len(images), _stream(stream)))
+
+
+def wsm_reduce_batch(h: Handle, images: list[dict], stream=None) -> list[int]:
+    """Unique colors of every image (dicts with rgb, colors, counts; colors and
+    counts hold n_pixels entries); sets each dict's n_unique and returns them."""
+    arr = (WsmItem * max(len(images), 1))()
+    for q, im in enumerate(images):
+        n, stride = _pixels(im["rgb"])
+        it = arr[q]
+        it.d_rgb = _dev(im["rgb"], torch.uint8, "rgb")
+        it.n_pixels = n
+        it.pixel_stride = stride
+        it.d_colors = _dev(im["colors"], torch.uint32, "colors", n)
+        it.d_counts = _dev(im["counts"], torch.uint32, "counts", n)
+    _check(lib().wsm_reduce_batch(h.ptr, C.cast(arr, C.c_void_p), len(images), _stream(stream)))
+    out = [int(arr[q].n_unique) for q in range(len(images))]
+    for im, nu in zip(images, out):
+        im["n_unique"] = nu
+    return out
+
+
+def wsm_init_batch(h: Handle, images: list[dict], seeds: list[int], stream=None):
+    """Initial centers and labels of every image (dicts with colors, n_unique,
+    K, centers, labels)."""
+    arr = (WsmItem * max(len(images), 1))()
+    for q, im in enumerate(images):
+        K, nu = int(im["K"]), int(im["n_unique"])
+        it = arr[q]
+        it.K = K
+        it.n_unique = nu
+        it.d_colors = _dev(im["colors"], torch.uint32, "colors", nu)
+        it.d_centers = _dev(im["centers"], torch.float32, "centers", 4 * K)
+        it.d_labels = _dev(im["labels"], torch.uint8, "labels", nu)
+    if len(seeds) != len(images):
+        raise ValueError("one seed per image")
+    sd = (C.c_uint64 * max(len(images), 1))(*[int(x) & (2**64 - 1) for x in seeds])
+    _check(lib().wsm_init_batch(h.ptr, C.cast(arr, C.c_void_p), len(images),
+                                C.cast(sd, C.c_void_p), _stream(stream)))
+
+
+def wsm_distortion_batch(h: Handle, images: list[dict], d_mse: torch.Tensor | None = None,
+                         sync: bool = True, stream=None):
+    """MSE of Eq. 2 of every image (dicts with rgb, K, centers, index); returns
+    the host floats if sync, else None."""
+    arr = (WsmItem * max(len(images), 1))()
+    for q, im in enumerate(images):
+        n, stride = _pixels(im["rgb"])
+        K = int(im["K"])
+        it = arr[q]
+        it.d_rgb = _dev(im["rgb"], torch.uint8, "rgb")
+        it.n_pixels = n
+        it.pixel_stride = stride
+        it.K = K
+        it.d_centers = _dev(im["centers"], torch.float32, "centers", 4 * K)
+        it.d_index = _dev(im["index"], torch.uint8, "index", n)
+    m = (C.c_double * max(len(images), 1))()
+    _check(lib().wsm_distortion_batch(h.ptr, C.cast(arr, C.c_void_p), len(images),
+                                      _dev(d_mse, torch.float64, "d_mse", len(images)),
+                                      C.cast(m, C.c_void_p) if sync else None,
+                                      _stream(stream)))
+    return [m[q] for q in range(len(images))] if sync else None
 
 
 def wsm_distortion(h: Handle, rgb: torch.Tensor, centers: torch.Tensor, K: int,

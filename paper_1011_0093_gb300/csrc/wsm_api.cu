@@ -93,13 +93,54 @@ __global__ void k_init(const uint32_t* __restrict__ colors, int64_t n_unique, in
     for (int64_t i = tid; i < n_unique; i += (int64_t)gridDim.x * blockDim.x) labels[i] = 0;
 }
 
+// The images of one initialisation launch: image i owns the blocks
+// [first_blk[i], first_blk[i+1]) and reads its K sampled indices at
+// pick + i * pick_stride.
+struct InitItems {
+    int n_items;
+    int first_blk[kMaxBatch + 1];
+    const uint32_t* colors[kMaxBatch];
+    int64_t n_unique[kMaxBatch];
+    int K[kMaxBatch];
+    float4* centers[kMaxBatch];
+    uint8_t* labels[kMaxBatch];
+    const uint32_t* pick;
+    int pick_stride;
+};
+
+__global__ void k_init_batch(const __grid_constant__ InitItems B) {
+    const int i = item_of_block(B.first_blk, B.n_items, blockIdx.x);
+    const int G = B.first_blk[i + 1] - B.first_blk[i];
+    const int64_t tid = (int64_t)(blockIdx.x - B.first_blk[i]) * blockDim.x + threadIdx.x;
+    if (tid < B.K[i]) {
+        const uint32_t c = B.colors[i][B.pick[(size_t)i * B.pick_stride + tid]];
+        B.centers[i][tid] = make_float4((float)((c >> 16) & 255u), (float)((c >> 8) & 255u),
+                                        (float)(c & 255u), 0.f);
+    }
+    for (int64_t q = tid; q < B.n_unique[i]; q += (int64_t)G * blockDim.x) B.labels[i][q] = 0;
+}
+
 int iterate_kernel_setup(wsm_handle* h);   // wsm_iterate.cu
 
 void free_slots(wsm_handle* h) {
-    void* ptrs[] = {h->tab, h->tab_nb, h->sums, h->sums64, h->acc, h->trace, h->lut,
-                    h->slot_ctrl};
+    void* ptrs[] = {h->tab,   h->tab_nb, h->sums,      h->sums64,   h->acc,       h->trace,
+                    h->lut,   h->slot_ctrl, h->hist,   h->bitmap,   h->blk_total, h->batch_nu,
+                    h->batch_mse, h->pick};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    void* host_ptrs[] = {h->host_nu, h->host_mse, h->host_pick};
+    for (void* p : host_ptrs)
+        if (p) cudaFreeHost(p);
+    h->hist = nullptr;
+    h->bitmap = nullptr;
+    h->blk_total = nullptr;
+    h->batch_nu = nullptr;
+    h->batch_mse = nullptr;
+    h->pick = nullptr;
+    h->host_nu = nullptr;
+    h->host_mse = nullptr;
+    h->host_pick = nullptr;
+    h->rslots = 0;
     h->tab = nullptr;
     h->tab_nb = nullptr;
     h->sums = nullptr;
@@ -111,10 +152,12 @@ void free_slots(wsm_handle* h) {
     h->slots = 0;
 }
 
-// Per-image scratch for `slots` images (replaces any previous slots).
+// Per-image scratch for `slots` images (replaces any previous slots), and
+// unique-color reduction scratch for min(slots, kReduceSlots) images.
 int alloc_slots(wsm_handle* h, int slots) {
     free_slots(h);
     const size_t kk = (size_t)h->max_K * h->max_K, n = (size_t)slots;
+    const size_t r = (size_t)std::min(slots, kReduceSlots);
     struct {
         void** p;
         size_t bytes;
@@ -127,6 +170,12 @@ int alloc_slots(wsm_handle* h, int slots) {
         {(void**)&h->trace, sizeof(double) * kMaxTrace * n},
         {(void**)&h->lut, (size_t)kHistBins * n},
         {(void**)&h->slot_ctrl, sizeof(Ctrl) * n},
+        {(void**)&h->hist, sizeof(uint32_t) * kHistBins * r},
+        {(void**)&h->bitmap, sizeof(uint32_t) * kMapWords * r},
+        {(void**)&h->blk_total, sizeof(uint32_t) * kScanBlocks * r},
+        {(void**)&h->batch_nu, sizeof(int64_t) * n},
+        {(void**)&h->batch_mse, sizeof(double) * n},
+        {(void**)&h->pick, sizeof(uint32_t) * (size_t)h->max_K * n},
     };
     for (auto& a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.bytes);
@@ -136,7 +185,25 @@ int alloc_slots(wsm_handle* h, int slots) {
                                          cudaGetErrorString(e));
         }
     }
+    struct {
+        void** p;
+        size_t bytes;
+    } host_allocs[] = {
+        {(void**)&h->host_nu, sizeof(int64_t) * n},
+        {(void**)&h->host_mse, sizeof(double) * n},
+        {(void**)&h->host_pick, sizeof(uint32_t) * (size_t)h->max_K * n},
+    };
+    for (auto& a : host_allocs) {
+        cudaError_t e = cudaMallocHost(a.p, a.bytes);
+        if (e != cudaSuccess) {
+            free_slots(h);
+            return fail(WSM_E_NOMEM, std::string("cudaMallocHost (image slots): ") +
+                                         cudaGetErrorString(e));
+        }
+    }
     cudaError_t e = cudaMemset(h->slot_ctrl, 0, sizeof(Ctrl) * n);
+    if (e == cudaSuccess) e = cudaMemset(h->hist, 0, sizeof(uint32_t) * kHistBins * r);
+    if (e == cudaSuccess) e = cudaMemset(h->bitmap, 0, sizeof(uint32_t) * kMapWords * r);
     if (e == cudaSuccess)
         e = cudaMemset(h->acc, 0, sizeof(unsigned long long) * 4 * (size_t)h->max_K * n);
     if (e != cudaSuccess) {
@@ -144,6 +211,7 @@ int alloc_slots(wsm_handle* h, int slots) {
         return cuda_fail(e, "slot initialisation");
     }
     h->slots = slots;
+    h->rslots = (int)r;
     return WSM_OK;
 }
 
@@ -182,9 +250,6 @@ extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64
         void** p;
         size_t bytes;
     } allocs[] = {
-        {(void**)&h->hist, sizeof(uint32_t) * kHistBins},
-        {(void**)&h->bitmap, sizeof(uint32_t) * kMapWords},
-        {(void**)&h->blk_total, sizeof(uint32_t) * kScanBlocks},
         {(void**)&h->mse_part, sizeof(double) * 1032},   // 1024 partials + result
         {(void**)&h->ctrl, sizeof(Ctrl)},
     };
@@ -205,8 +270,7 @@ extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64
         wsm_destroy(h);
         return fail(WSM_E_NOMEM, "cudaMallocHost failed");
     }
-    e = cudaMemset(h->hist, 0, sizeof(uint32_t) * kHistBins);
-    if (e == cudaSuccess) e = cudaMemset(h->bitmap, 0, sizeof(uint32_t) * kMapWords);
+    e = cudaEventCreateWithFlags(&h->pick_ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(h->ctrl, 0, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -224,10 +288,11 @@ extern "C" int wsm_destroy(wsm_handle* h) {
     if (h->device >= 0 && prev != h->device) cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     free_slots(h);
-    void* dev_ptrs[] = {h->hist, h->bitmap, h->blk_total, h->mse_part, h->ctrl};
+    void* dev_ptrs[] = {h->mse_part, h->ctrl};
     for (void* p : dev_ptrs)
         if (p) cudaFree(p);
     if (h->host_ctrl) cudaFreeHost(h->host_ctrl);
+    if (h->pick_ready) cudaEventDestroy(h->pick_ready);
     if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
     delete h;
     return WSM_OK;
@@ -273,5 +338,58 @@ extern "C" int wsm_init(wsm_handle* h, const uint32_t* d_colors, int64_t n_uniqu
                                                           (float4*)d_centers, d_labels);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_init launch");
+    return WSM_OK;
+}
+
+extern "C" int wsm_init_batch(wsm_handle* h, const wsm_item* items, int n_items,
+                              const uint64_t* seeds, wsm_stream stream) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (n_items < 0 || (n_items > 0 && (!items || !seeds))) return fail(WSM_E_INVAL, "bad item list");
+    if (n_items > h->slots)
+        return fail(WSM_E_INVAL, "more items than reserved slots (wsm_reserve_batch)");
+    for (int i = 0; i < n_items; ++i) {
+        const wsm_item& it = items[i];
+        if (it.K < 1 || it.K > h->max_K) return fail(WSM_E_INVAL, "K out of [1, max_K]");
+        if (it.n_unique < it.K || it.n_unique > h->max_unique)
+            return fail(WSM_E_INVAL, "n_unique must be in [K, max_unique]");
+        if (!it.d_colors || !it.d_centers || !it.d_labels)
+            return fail(WSM_E_INVAL, "null device pointer");
+        if ((uintptr_t)it.d_centers & 15) return fail(WSM_E_INVAL, "centers must be 16-byte aligned");
+    }
+    if (n_items == 0) return WSM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the previous call's copy out of the staging buffer must be done
+    cudaError_t e = cudaEventSynchronize(h->pick_ready);
+    if (e != cudaSuccess) return cuda_fail(e, "staging buffer wait");
+    for (int i = 0; i < n_items; ++i) {
+        std::vector<int64_t> pick = floyd_sample(items[i].n_unique, items[i].K, seeds[i]);
+        for (int k = 0; k < items[i].K; ++k)
+            h->host_pick[(size_t)i * h->max_K + k] = (uint32_t)pick[k];
+    }
+    e = cudaMemcpyAsync(h->pick, h->host_pick, sizeof(uint32_t) * (size_t)h->max_K * n_items,
+                        cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(h->pick_ready, s);
+    if (e != cudaSuccess) return cuda_fail(e, "initial index copy");
+    for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
+        InitItems B;
+        B.n_items = std::min(kMaxBatch, n_items - i0);
+        B.pick = h->pick + (size_t)i0 * h->max_K;
+        B.pick_stride = h->max_K;
+        B.first_blk[0] = 0;
+        for (int q = 0; q < B.n_items; ++q) {
+            const wsm_item& it = items[i0 + q];
+            B.colors[q] = it.d_colors;
+            B.n_unique[q] = it.n_unique;
+            B.K[q] = it.K;
+            B.centers[q] = reinterpret_cast<float4*>(it.d_centers);
+            B.labels[q] = it.d_labels;
+            const int64_t want = (it.n_unique + 255) / 256;   // >= 1 block, covers K <= N'
+            B.first_blk[q + 1] = B.first_blk[q] + (int)std::min<int64_t>(want, 64);
+        }
+        k_init_batch<<<B.first_blk[B.n_items], 256, 0, s>>>(B);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "init launch");
+    }
     return WSM_OK;
 }

@@ -33,6 +33,7 @@ constexpr int kMaxTrace = 4096;              // SSE values kept per wsm_iterate 
 constexpr int kCopies = 8;                   // replicas of the global accumulators
 constexpr int kChunk = 32;                   // colors per warp chunk (one per lane)
 constexpr int kMaxBatch = 48;                // images per persistent launch
+constexpr int kReduceSlots = 16;             // images per unique-color reduction launch
 
 // Control words in device memory (one block per handle).
 // The fields before `status` are cleared before every persistent launch, so
@@ -60,12 +61,15 @@ struct wsm_handle {
     int iter_grid = 0;           // co-resident blocks of the persistent kernel
     int iter_blocks_per_sm = 0;
     // scratch (device)
-    uint32_t* hist = nullptr;    // [2^24] zero between calls
-    uint32_t* bitmap = nullptr;  // [2^19] zero between calls
-    uint32_t* blk_total = nullptr;   // [kScanBlocks]
     double* mse_part = nullptr;  // [1024] block partials + [1] result
     wsm::Ctrl* ctrl = nullptr;   // status word, N', MSE mirror
     wsm::Ctrl* host_ctrl = nullptr;  // pinned mirror for status reads
+    cudaEvent_t pick_ready = nullptr;  // host_pick may be rewritten once this has fired
+    // unique-color reduction scratch, one slot per image of a reduction launch
+    int rslots = 0;
+    uint32_t* hist = nullptr;    // [rslots][2^24] zero between calls
+    uint32_t* bitmap = nullptr;  // [rslots][2^19] zero between calls
+    uint32_t* blk_total = nullptr;   // [rslots][kScanBlocks]
     // per-image scratch of the persistent kernel, one slot per image of a batch
     int slots = 0;
     float4* tab = nullptr;       // [slots][max_K^2] sorted rows: (d/4, c.x, c.y, c.z)
@@ -76,6 +80,12 @@ struct wsm_handle {
     double* trace = nullptr;     // [slots][kMaxTrace]
     uint8_t* lut = nullptr;      // [slots][2^24] color -> label
     wsm::Ctrl* slot_ctrl = nullptr;  // [slots] barrier counter, iterations, distances
+    int64_t* batch_nu = nullptr;     // [slots] N' of each image of the last wsm_reduce_batch
+    double* batch_mse = nullptr;     // [slots] MSE of each image of the last wsm_distortion_batch
+    uint32_t* pick = nullptr;        // [slots][max_K] initial center indices (wsm_init_batch)
+    int64_t* host_nu = nullptr;      // pinned mirrors of the three arrays above
+    double* host_mse = nullptr;
+    uint32_t* host_pick = nullptr;
 };
 
 namespace wsm {
@@ -138,6 +148,26 @@ __device__ __forceinline__ bool grid_sync(unsigned* counter, unsigned* status, u
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Packed key 0x00RRGGBB of pixel p of an image stored as [n][stride] bytes
+// (R, G, B first; a fourth byte per pixel is ignored).
+__device__ __forceinline__ uint32_t pixel_key(const uint8_t* __restrict__ rgb, int64_t p,
+                                              int stride) {
+    if (stride == 4) {
+        uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(rgb) + p);
+        return ((v & 0xFFu) << 16) | (v & 0xFF00u) | ((v >> 16) & 0xFFu);
+    }
+    const uint8_t* q = rgb + 3 * p;
+    return ((uint32_t)__ldg(q) << 16) | ((uint32_t)__ldg(q + 1) << 8) | (uint32_t)__ldg(q + 2);
+}
+
+// Index of the item that owns block `blk` when item i owns the blocks
+// [first[i], first[i+1]) (ranges may be empty).
+__device__ __forceinline__ int item_of_block(const int* first, int n_items, int blk) {
+    int i = 0;
+    while (i + 1 < n_items && blk >= first[i + 1]) ++i;
+    return i;
 }
 
 // Squared distance in the difference form with one fixed rounding order

@@ -18,21 +18,12 @@ int launch_sortmeans(wsm_handle* h, bool map_mode, const uint32_t* colors, const
 int check_item(wsm_handle* h, const wsm_item& it, bool need_pixels, bool need_counts);
 int launch_map_items(wsm_handle* h, const wsm_item* items, int n_items, int slot0, cudaStream_t s);
 
-__device__ __forceinline__ uint32_t key_of(const uint8_t* __restrict__ rgb, int64_t p, int stride) {
-    if (stride == 4) {
-        uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(rgb) + p);
-        return ((v & 0xFFu) << 16) | (v & 0xFF00u) | ((v >> 16) & 0xFFu);
-    }
-    const uint8_t* q = rgb + 3 * p;
-    return ((uint32_t)__ldg(q) << 16) | ((uint32_t)__ldg(q + 1) << 8) | (uint32_t)__ldg(q + 2);
-}
-
 __global__ void __launch_bounds__(256) k_gather(const uint8_t* __restrict__ rgb, int64_t n,
                                                 int stride, const uint8_t* __restrict__ lut,
                                                 uint8_t* __restrict__ index) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x)
-        index[p] = lut[key_of(rgb, p, stride)];
+        index[p] = lut[pixel_key(rgb, p, stride)];
 }
 
 // The gather of a batch: image i owns blocks [first_blk[i], first_blk[i+1])
@@ -49,14 +40,13 @@ struct GatherBatch {
 };
 
 __global__ void __launch_bounds__(256) k_gather_batch(const __grid_constant__ GatherBatch B) {
-    int i = 0;
-    while (i + 1 < B.n_items && (int)blockIdx.x >= B.first_blk[i + 1]) ++i;
+    const int i = item_of_block(B.first_blk, B.n_items, blockIdx.x);
     const int g0 = B.first_blk[i], G = B.first_blk[i + 1] - g0;
     const uint8_t* lut = B.lut + (size_t)B.slot[i] * kHistBins;
     const int64_t n = B.n[i];
     for (int64_t p = (int64_t)(blockIdx.x - g0) * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)G * blockDim.x)
-        B.index[i][p] = lut[key_of(B.rgb[i], p, B.stride[i])];
+        B.index[i][p] = lut[pixel_key(B.rgb[i], p, B.stride[i])];
 }
 
 constexpr int kMseThreads = 256;
@@ -95,7 +85,7 @@ __global__ void __launch_bounds__(kMseThreads) k_mse_partial(
             bad = true;
             continue;
         }
-        const uint32_t key = key_of(rgb, p, stride);
+        const uint32_t key = pixel_key(rgb, p, stride);
         const float4 c = s_c[k];
         acc += to_fixed20(sq3((float)((key >> 16) & 255u), (float)((key >> 8) & 255u),
                               (float)(key & 255u), c.x, c.y, c.z));
@@ -121,6 +111,73 @@ __global__ void k_mse_final(const unsigned long long* __restrict__ part, int npa
         const double m = n > 0 ? (double)t * (1.0 / 1048576.0) / (double)n : 0.0;
         *out = m;
         if (out2) *out2 = m;
+    }
+}
+
+// The images of one distortion launch: image i owns the partial-sum blocks
+// [first_blk[i], first_blk[i+1]).
+struct MseItems {
+    int n_items;
+    int first_blk[kMaxBatch + 1];
+    const uint8_t* rgb[kMaxBatch];
+    int64_t n[kMaxBatch];
+    int stride[kMaxBatch];
+    const float4* centers[kMaxBatch];
+    int K[kMaxBatch];
+    const uint8_t* index[kMaxBatch];
+    double* out[kMaxBatch];     // MSE (device), always written
+    double* user[kMaxBatch];    // MSE (device), a caller's copy, may be null
+    unsigned long long* part;   // one partial sum per block of the launch
+    unsigned* status;
+};
+
+// Per-block fixed-point sums as in k_mse_partial, for the image owning the block.
+__global__ void __launch_bounds__(kMseThreads) k_mse_partial_batch(const __grid_constant__ MseItems B) {
+    __shared__ float4 s_c[WSM_MAX_K];
+    __shared__ unsigned long long s_red[kMseThreads / 32];
+    const int i = item_of_block(B.first_blk, B.n_items, blockIdx.x);
+    const int g = blockIdx.x - B.first_blk[i], G = B.first_blk[i + 1] - B.first_blk[i];
+    const int K = B.K[i];
+    const uint8_t* rgb = B.rgb[i];
+    const uint8_t* index = B.index[i];
+    const int64_t n = B.n[i];
+    const int stride = B.stride[i];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) s_c[k] = B.centers[i][k];
+    __syncthreads();
+    unsigned long long acc = 0;
+    bool bad = false;
+    for (int64_t p = (int64_t)g * blockDim.x + threadIdx.x; p < n; p += (int64_t)G * blockDim.x) {
+        const int k = index[p];
+        if (k >= K) {
+            bad = true;
+            continue;
+        }
+        const uint32_t key = pixel_key(rgb, p, stride);
+        const float4 c = s_c[k];
+        acc += to_fixed20(sq3((float)((key >> 16) & 255u), (float)((key >> 8) & 255u),
+                              (float)(key & 255u), c.x, c.y, c.z));
+    }
+    if (bad) atomicOr(B.status, ST_BAD_LABEL);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kMseThreads / 32; ++w) t += s_red[w];
+        B.part[blockIdx.x] = t;
+    }
+}
+
+// One warp per image adds its blocks' sums and writes MSE = total * 2^-20 / N.
+__global__ void k_mse_final_batch(const __grid_constant__ MseItems B) {
+    const int i = blockIdx.x;
+    unsigned long long t = 0;
+    for (int q = B.first_blk[i] + threadIdx.x; q < B.first_blk[i + 1]; q += 32) t += B.part[q];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+    if (threadIdx.x == 0) {
+        const double m = (double)t * (1.0 / 1048576.0) / (double)B.n[i];
+        *B.out[i] = m;
+        if (B.user[i]) *B.user[i] = m;
     }
 }
 
@@ -229,6 +286,68 @@ extern "C" int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pix
         rc = read_status(h, s);
         *mse = h->host_ctrl->mse;
         if (rc != WSM_OK) return rc;
+    }
+    return WSM_OK;
+}
+
+extern "C" int wsm_distortion_batch(wsm_handle* h, const wsm_item* items, int n_items,
+                                    double* d_mse, double* mse, wsm_stream stream) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (n_items < 0 || (n_items > 0 && !items)) return fail(WSM_E_INVAL, "bad item list");
+    if (n_items > h->slots)
+        return fail(WSM_E_INVAL, "more items than reserved slots (wsm_reserve_batch)");
+    for (int i = 0; i < n_items; ++i) {
+        const wsm_item& it = items[i];
+        if (it.pixel_stride != 3 && it.pixel_stride != 4)
+            return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
+        if (it.n_pixels < 1 || it.n_pixels > h->max_pixels)
+            return fail(WSM_E_INVAL, "n_pixels must be in [1, max_pixels]");
+        if (it.K < 1 || it.K > WSM_MAX_K) return fail(WSM_E_INVAL, "K out of [1, 256]");
+        if (!it.d_rgb || !it.d_index || !it.d_centers) return fail(WSM_E_INVAL, "null device pointer");
+        if ((uintptr_t)it.d_centers & 15) return fail(WSM_E_INVAL, "centers must be 16-byte aligned");
+        if (it.pixel_stride == 4 && ((uintptr_t)it.d_rgb & 3))
+            return fail(WSM_E_INVAL, "4-byte pixels must be 4-byte aligned");
+    }
+    if (n_items == 0) return WSM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
+        MseItems B;
+        B.n_items = std::min(kMaxBatch, n_items - i0);
+        B.part = reinterpret_cast<unsigned long long*>(h->mse_part);
+        B.status = &h->ctrl->status;
+        int64_t total = 0;
+        for (int q = 0; q < B.n_items; ++q) total += items[i0 + q].n_pixels;
+        // at most 4 blocks per SM in all (and no more than the partial-sum
+        // buffer holds), split in proportion to pixels, >= 1 block per image
+        const int64_t budget = std::min<int64_t>(kMseMaxBlocks - kMaxBatch, 4 * (int64_t)h->sms);
+        B.first_blk[0] = 0;
+        for (int q = 0; q < B.n_items; ++q) {
+            const wsm_item& it = items[i0 + q];
+            B.rgb[q] = it.d_rgb;
+            B.n[q] = it.n_pixels;
+            B.stride[q] = it.pixel_stride;
+            B.centers[q] = reinterpret_cast<const float4*>(it.d_centers);
+            B.K[q] = it.K;
+            B.index[q] = it.d_index;
+            B.out[q] = h->batch_mse + i0 + q;
+            B.user[q] = d_mse ? d_mse + i0 + q : nullptr;
+            const int64_t want = (it.n_pixels + 4 * kMseThreads - 1) / (4 * kMseThreads);
+            const int64_t share = std::max<int64_t>(1, budget * it.n_pixels / total);
+            B.first_blk[q + 1] = B.first_blk[q] + (int)std::min(want, share);
+        }
+        k_mse_partial_batch<<<B.first_blk[B.n_items], kMseThreads, 0, s>>>(B);
+        k_mse_final_batch<<<B.n_items, 32, 0, s>>>(B);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "distortion launch");
+    }
+    if (mse) {
+        cudaError_t e = cudaMemcpyAsync(h->host_mse, h->batch_mse, sizeof(double) * n_items,
+                                        cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "mse copy");
+        rc = read_status(h, s);
+        if (rc != WSM_OK) return rc;
+        for (int i = 0; i < n_items; ++i) mse[i] = h->host_mse[i];
     }
     return WSM_OK;
 }

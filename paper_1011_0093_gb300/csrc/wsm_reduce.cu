@@ -14,25 +14,40 @@
 
 namespace wsm {
 
-// Packed key 0x00RRGGBB of pixel p.
-__device__ __forceinline__ uint32_t pixel_key(const uint8_t* __restrict__ rgb, int64_t p,
-                                              int stride) {
-    if (stride == 4) {
-        uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(rgb) + p);
-        return ((v & 0xFFu) << 16) | (v & 0xFF00u) | ((v >> 16) & 0xFFu);
-    }
-    const uint8_t* q = rgb + 3 * p;
-    return ((uint32_t)__ldg(q) << 16) | ((uint32_t)__ldg(q + 1) << 8) | (uint32_t)__ldg(q + 2);
-}
+// The images of one reduction launch: image i uses reduction slot i (its own
+// histogram, occupancy map and block totals), owns the histogram blocks
+// [first_blk[i], first_blk[i+1]) and the compaction blocks
+// [i * kScanBlocks, (i+1) * kScanBlocks).
+struct ReduceItems {
+    int n_items;
+    int first_blk[kReduceSlots + 1];
+    const uint8_t* rgb[kReduceSlots];
+    int64_t n[kReduceSlots];
+    int stride[kReduceSlots];
+    uint32_t* colors[kReduceSlots];
+    uint32_t* counts[kReduceSlots];
+    int64_t capacity[kReduceSlots];
+    int64_t* n_out[kReduceSlots];    // N' (device), always written
+    int64_t* n_user[kReduceSlots];   // N' (device), a caller's copy, may be null
+    uint32_t* hist;                  // slot i at hist + i * 2^24
+    uint32_t* bitmap;                // slot i at bitmap + i * 2^19
+    uint32_t* blk_total;             // slot i at blk_total + i * kScanBlocks
+    unsigned* status;
+};
 
 // Histogram with warp aggregation: lanes holding the same color elect one
 // leader, which adds the group's size with a single atomic.
-__global__ void __launch_bounds__(256) k_hist24(const uint8_t* __restrict__ rgb, int64_t n,
-                                                int stride, uint32_t* __restrict__ hist,
-                                                uint32_t* __restrict__ bitmap) {
+__global__ void __launch_bounds__(256) k_hist24(const __grid_constant__ ReduceItems R) {
+    const int i = item_of_block(R.first_blk, R.n_items, blockIdx.x);
+    const int g = blockIdx.x - R.first_blk[i], G = R.first_blk[i + 1] - R.first_blk[i];
+    const uint8_t* rgb = R.rgb[i];
+    const int64_t n = R.n[i];
+    const int stride = R.stride[i];
+    uint32_t* hist = R.hist + (size_t)i * kHistBins;
+    uint32_t* bitmap = R.bitmap + (size_t)i * kMapWords;
     const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp = ((int64_t)g * blockDim.x + threadIdx.x) >> 5;
+    const int64_t warps = ((int64_t)G * blockDim.x) >> 5;
     for (int64_t base = warp * 32; base < n; base += warps * 32) {
         int64_t p = base + lane;
         bool valid = p < n;
@@ -46,10 +61,11 @@ __global__ void __launch_bounds__(256) k_hist24(const uint8_t* __restrict__ rgb,
 }
 
 // Pass 1 of the compaction: the number of set bits in each block's 2048 words.
-__global__ void __launch_bounds__(kScanThreads) k_scan_count(const uint32_t* __restrict__ bitmap,
-                                                             uint32_t* __restrict__ blk_total) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_count(const __grid_constant__ ReduceItems R) {
+    const int i = blockIdx.x / kScanBlocks, b = blockIdx.x % kScanBlocks;
+    const uint32_t* bitmap = R.bitmap + (size_t)i * kMapWords;
     const uint4 a = reinterpret_cast<const uint4*>(bitmap)[
-        ((size_t)blockIdx.x * kScanWordsPerBlock + threadIdx.x * kScanWordsPerThread) / 4];
+        ((size_t)b * kScanWordsPerBlock + threadIdx.x * kScanWordsPerThread) / 4];
     unsigned c = __popc(a.x) + __popc(a.y) + __popc(a.z) + __popc(a.w);
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
     __shared__ unsigned s_w[kScanThreads / 32];
@@ -57,8 +73,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_count(const uint32_t* __r
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned t = 0;
-        for (int i = 0; i < kScanThreads / 32; ++i) t += s_w[i];
-        blk_total[blockIdx.x] = t;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += s_w[w];
+        R.blk_total[(size_t)i * kScanBlocks + b] = t;
     }
 }
 
@@ -68,30 +84,33 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_count(const uint32_t* __r
 // time, lane l handles bit l (so the 32 bins of a word are read and cleared
 // with one coalesced access), kEmitBatch words in flight per warp.  Output
 // order is ascending color order.
-__global__ void __launch_bounds__(kScanThreads) k_scan_emit(
-    uint32_t* __restrict__ bitmap, uint32_t* __restrict__ hist,
-    const uint32_t* __restrict__ blk_total, uint32_t* __restrict__ colors,
-    uint32_t* __restrict__ counts, int64_t capacity, int64_t* __restrict__ d_n_unique,
-    Ctrl* __restrict__ ctrl) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_emit(const __grid_constant__ ReduceItems R) {
     __shared__ uint32_t s_word[kScanWordsPerBlock];
     __shared__ uint32_t s_off[kScanWordsPerBlock];
     __shared__ unsigned s_w[kScanThreads / 32];
     __shared__ unsigned long long s_base;
+    const int item = blockIdx.x / kScanBlocks, b = blockIdx.x % kScanBlocks;
+    uint32_t* bitmap = R.bitmap + (size_t)item * kMapWords;
+    uint32_t* hist = R.hist + (size_t)item * kHistBins;
+    const uint32_t* blk_total = R.blk_total + (size_t)item * kScanBlocks;
+    uint32_t* colors = R.colors[item];
+    uint32_t* counts = R.counts[item];
+    const int64_t capacity = R.capacity[item];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    // offset of this block: sum of the totals of blocks [0, blockIdx.x)
+    // offset of this block: sum of the totals of blocks [0, b)
     unsigned long long before = 0;
-    for (int i = tid; i < (int)blockIdx.x; i += kScanThreads) before += blk_total[i];
+    for (int q = tid; q < b; q += kScanThreads) before += blk_total[q];
     for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xFFFFFFFFu, before, o);
     if (tid == 0) s_base = 0;
     __syncthreads();
     if (lane == 0 && before) atomicAdd(&s_base, before);
-    const size_t w0 = (size_t)blockIdx.x * kScanWordsPerBlock;
+    const size_t w0 = (size_t)b * kScanWordsPerBlock;
     uint4* wv = reinterpret_cast<uint4*>(bitmap + w0) + tid;
     const uint4 a = wv[0];
     const uint32_t words[4] = {a.x, a.y, a.z, a.w};
     unsigned mine = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) mine += __popc(words[i]);
+    for (int q = 0; q < 4; ++q) mine += __popc(words[q]);
     // block-wide exclusive scan of `mine`
     unsigned incl = mine;
     for (int o = 1; o < 32; o <<= 1) {
@@ -101,13 +120,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_emit(
     if (lane == 31) s_w[wid] = incl;
     __syncthreads();
     unsigned warp_off = 0;
-    for (int i = 0; i < wid; ++i) warp_off += s_w[i];
+    for (int q = 0; q < wid; ++q) warp_off += s_w[q];
     unsigned off = warp_off + (incl - mine);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        s_word[4 * tid + i] = words[i];
-        s_off[4 * tid + i] = off;
-        off += __popc(words[i]);
+    for (int q = 0; q < 4; ++q) {
+        s_word[4 * tid + q] = words[q];
+        s_off[4 * tid + q] = off;
+        off += __popc(words[q]);
     }
     if (a.x | a.y | a.z | a.w) wv[0] = make_uint4(0, 0, 0, 0);
     __syncthreads();
@@ -137,12 +156,37 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_emit(
             }
         }
     }
-    if (blockIdx.x == gridDim.x - 1 && tid == kScanThreads - 1) {
+    if (b == kScanBlocks - 1 && tid == kScanThreads - 1) {
         const int64_t total = base + off;   // the last thread of the last block ends at N'
-        ctrl->n_unique = total;
-        if (d_n_unique) *d_n_unique = total;
-        if (total > capacity) atomicOr(&ctrl->status, ST_CAPACITY);
+        *R.n_out[item] = total;
+        if (R.n_user[item]) *R.n_user[item] = total;
+        if (total > capacity) atomicOr(R.status, ST_CAPACITY);
     }
+}
+
+// Launch the three reduction kernels for R.n_items images whose per-image
+// fields are filled in; sets the scratch pointers and the histogram blocks.
+static int launch_reduce(wsm_handle* h, ReduceItems& R, cudaStream_t s) {
+    R.hist = h->hist;
+    R.bitmap = h->bitmap;
+    R.blk_total = h->blk_total;
+    R.status = &h->ctrl->status;
+    int64_t total = 0;
+    for (int i = 0; i < R.n_items; ++i) total += R.n[i];
+    // at most 8 blocks of 256 per SM in all, split in proportion to pixels
+    const int64_t budget = (int64_t)h->sms * 8;
+    R.first_blk[0] = 0;
+    for (int i = 0; i < R.n_items; ++i) {
+        const int64_t want = (R.n[i] + 255) / 256;
+        const int64_t share = std::max<int64_t>(1, budget * R.n[i] / std::max<int64_t>(total, 1));
+        R.first_blk[i + 1] = R.first_blk[i] + (int)(R.n[i] > 0 ? std::min(want, share) : 0);
+    }
+    if (R.first_blk[R.n_items] > 0) k_hist24<<<R.first_blk[R.n_items], 256, 0, s>>>(R);
+    k_scan_count<<<kScanBlocks * R.n_items, kScanThreads, 0, s>>>(R);
+    k_scan_emit<<<kScanBlocks * R.n_items, kScanThreads, 0, s>>>(R);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "reduce launch");
+    return WSM_OK;
 }
 
 }  // namespace wsm
@@ -163,17 +207,19 @@ extern "C" int wsm_reduce(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels,
     if (pixel_stride == 4 && ((uintptr_t)d_rgb & 3))
         return fail(WSM_E_INVAL, "4-byte pixels must be 4-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
-    if (n_pixels > 0) {
-        int64_t warps_needed = (n_pixels + 31) / 32;
-        int64_t blocks = (warps_needed + 7) / 8;
-        int grid = (int)std::min<int64_t>(blocks, (int64_t)h->sms * 8);
-        k_hist24<<<grid, 256, 0, s>>>(d_rgb, n_pixels, pixel_stride, h->hist, h->bitmap);
-    }
-    k_scan_count<<<kScanBlocks, kScanThreads, 0, s>>>(h->bitmap, h->blk_total);
-    k_scan_emit<<<kScanBlocks, kScanThreads, 0, s>>>(h->bitmap, h->hist, h->blk_total, d_colors,
-                                                    d_counts, capacity, d_n_unique, h->ctrl);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "reduce launch");
+    ReduceItems R;
+    R.n_items = 1;
+    R.rgb[0] = d_rgb;
+    R.n[0] = n_pixels;
+    R.stride[0] = pixel_stride;
+    R.colors[0] = d_colors;
+    R.counts[0] = d_counts;
+    R.capacity[0] = capacity;
+    R.n_out[0] = &h->ctrl->n_unique;
+    R.n_user[0] = d_n_unique;
+    rc = launch_reduce(h, R, s);
+    if (rc != WSM_OK) return rc;
+    cudaError_t e;
     if (n_unique) {
         e = cudaMemcpyAsync(&h->host_ctrl->n_unique, &h->ctrl->n_unique, sizeof(int64_t),
                             cudaMemcpyDeviceToHost, s);
@@ -182,5 +228,49 @@ extern "C" int wsm_reduce(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels,
         *n_unique = h->host_ctrl->n_unique;
         if (rc != WSM_OK) return rc;
     }
+    return WSM_OK;
+}
+
+extern "C" int wsm_reduce_batch(wsm_handle* h, wsm_item* items, int n_items, wsm_stream stream) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (n_items < 0 || (n_items > 0 && !items)) return fail(WSM_E_INVAL, "bad item list");
+    if (n_items > h->slots)
+        return fail(WSM_E_INVAL, "more items than reserved slots (wsm_reserve_batch)");
+    for (int i = 0; i < n_items; ++i) {
+        const wsm_item& it = items[i];
+        if (it.pixel_stride != 3 && it.pixel_stride != 4)
+            return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
+        if (it.n_pixels < 1 || it.n_pixels > h->max_pixels)
+            return fail(WSM_E_INVAL, "n_pixels must be in [1, max_pixels]");
+        if (!it.d_rgb || !it.d_colors || !it.d_counts) return fail(WSM_E_INVAL, "null device pointer");
+        if (it.pixel_stride == 4 && ((uintptr_t)it.d_rgb & 3))
+            return fail(WSM_E_INVAL, "4-byte pixels must be 4-byte aligned");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i0 = 0; i0 < n_items; i0 += h->rslots) {
+        ReduceItems R;
+        R.n_items = std::min(h->rslots, n_items - i0);
+        for (int q = 0; q < R.n_items; ++q) {
+            const wsm_item& it = items[i0 + q];
+            R.rgb[q] = it.d_rgb;
+            R.n[q] = it.n_pixels;
+            R.stride[q] = it.pixel_stride;
+            R.colors[q] = const_cast<uint32_t*>(it.d_colors);
+            R.counts[q] = const_cast<uint32_t*>(it.d_counts);
+            R.capacity[q] = it.n_pixels;
+            R.n_out[q] = h->batch_nu + i0 + q;
+            R.n_user[q] = nullptr;
+        }
+        rc = launch_reduce(h, R, s);
+        if (rc != WSM_OK) return rc;
+    }
+    if (n_items == 0) return WSM_OK;
+    cudaError_t e = cudaMemcpyAsync(h->host_nu, h->batch_nu, sizeof(int64_t) * n_items,
+                                    cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "n_unique copy");
+    rc = read_status(h, s);
+    if (rc != WSM_OK) return rc;
+    for (int i = 0; i < n_items; ++i) items[i].n_unique = h->host_nu[i];
     return WSM_OK;
 }

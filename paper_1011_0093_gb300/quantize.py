@@ -55,37 +55,36 @@ def quantize(rgb: torch.Tensor, K: int, seed: int = 0, max_iter: int = 10, eps: 
 
 def quantize_batch(images: list, K: int, seeds: list, max_iter: int = 10, eps: float = 0.0,
                    handle: N.Handle | None = None, mse: bool = True, stream=None) -> list:
-    """Quantize several uint8 [H, W, 3|4] CUDA images to K colors each, with
-    all their Sort-Means iterations in one persistent launch (per 48 images)
-    and all their final mappings in another."""
+    """Quantize several uint8 [H, W, 3|4] CUDA images to K colors each: one
+    batched call per step of the path (unique colors, initialisation, the
+    Sort-Means iterations in one persistent launch per 48 images, mapping,
+    MSE), with the results of quantize() image by image."""
     if handle is None:
         biggest = max(int(im.shape[0]) * int(im.shape[1]) for im in images)
         handle = N.Handle(K, biggest, biggest)
     N.wsm_reserve_batch(handle, len(images))
     items = []
-    for rgb, seed in zip(images, seeds):
+    for rgb in images:
         if not rgb.is_cuda or rgb.dtype != torch.uint8 or rgb.dim() != 3:
             raise ValueError("each image must be a uint8 CUDA tensor of shape [H, W, 3|4]")
         rgb = rgb.contiguous()
         H, W, _ = rgb.shape
         n = H * W
         dev = rgb.device
-        colors = torch.empty(n, dtype=torch.uint32, device=dev)
-        counts = torch.empty(n, dtype=torch.uint32, device=dev)
-        nu = N.wsm_reduce(handle, rgb, colors, counts, stream=stream)
-        colors, counts = colors[:nu], counts[:nu]
-        centers = torch.empty((K, 4), dtype=torch.float32, device=dev)
-        labels = torch.empty(nu, dtype=torch.uint8, device=dev)
-        N.wsm_init(handle, colors, nu, K, seed, centers, labels, stream=stream)
-        index = torch.empty((H, W), dtype=torch.uint8, device=dev)
-        items.append(dict(rgb=rgb, colors=colors, counts=counts, n_unique=nu, K=K,
-                          centers=centers, labels=labels, index=index))
+        items.append(dict(rgb=rgb, K=K,
+                          colors=torch.empty(n, dtype=torch.uint32, device=dev),
+                          counts=torch.empty(n, dtype=torch.uint32, device=dev),
+                          centers=torch.empty((K, 4), dtype=torch.float32, device=dev),
+                          labels=torch.empty(n, dtype=torch.uint8, device=dev),
+                          index=torch.empty((H, W), dtype=torch.uint8, device=dev)))
+    N.wsm_reduce_batch(handle, items, stream=stream)
+    N.wsm_init_batch(handle, items, seeds, stream=stream)
     iters = N.wsm_iterate_batch(handle, items, max_iter, eps, stream=stream)
     N.wsm_map_batch(handle, items, stream=stream)
+    mses = N.wsm_distortion_batch(handle, items, stream=stream) if mse else [None] * len(items)
     out = []
-    for it, done in zip(items, iters):
-        m = N.wsm_distortion(handle, it["rgb"], it["centers"], K, it["index"],
-                             stream=stream) if mse else None
-        out.append(Quantized(it["centers"], it["index"], it["colors"], it["counts"],
-                             it["labels"], it["n_unique"], done, [], m))
+    for it, done, m in zip(items, iters, mses):
+        nu = it["n_unique"]
+        out.append(Quantized(it["centers"], it["index"], it["colors"][:nu], it["counts"][:nu],
+                             it["labels"][:nu], nu, done, [], m))
     return out

@@ -107,3 +107,80 @@ def test_batch_rejects_more_items_than_slots(wsm):
         items = [prepare(wsm, h, img, 4, q) for q in range(2)]
         with pytest.raises(wsm.WsmError, match="slots"):
             wsm.wsm_iterate_batch(h, items, 5, 0.0)
+
+
+def test_reduce_init_distortion_batch_equal_single_calls(wsm):
+    """wsm_reduce_batch, wsm_init_batch and wsm_distortion_batch give each
+    image what wsm_reduce, wsm_init and wsm_distortion give it, bit for bit,
+    over 21 images (two reduction launches of at most 16), 3- and 4-byte
+    pixels, and images with one color or every pixel distinct."""
+    imgs = [synth.image(hh, ww, 300 + q, q % 11) for q, (hh, ww) in
+            enumerate([(512, 512), (256, 256), (96, 80), (300, 211), (64, 64), (700, 300),
+                       (40, 37), (128, 96), (17, 3), (200, 200), (33, 65), (256, 128),
+                       (90, 90), (48, 160), (120, 77), (64, 256), (31, 31), (150, 100)])]
+    imgs.append(np.full((20, 30, 3), 77, np.uint8))                        # one color
+    ramp = np.arange(64 * 64, dtype=np.uint32) * 4099
+    imgs.append(np.stack([ramp >> 16, (ramp >> 8) & 255, ramp & 255], -1)
+                .astype(np.uint8).reshape(64, 64, 3))                      # all distinct
+    rgba = np.concatenate([synth.image(100, 90, 9, 9), np.full((100, 90, 1), 255, np.uint8)], -1)
+    imgs.append(rgba)                                                      # 4-byte pixels
+    seeds = [1000 + 17 * q for q in range(len(imgs))]
+    with wsm.Handle(256, 512 * 512) as h:
+        wsm.wsm_reserve_batch(h, len(imgs))
+        batch = []
+        for img in imgs:
+            n = img.shape[0] * img.shape[1]
+            batch.append(dict(rgb=torch.from_numpy(np.ascontiguousarray(img)).cuda(),
+                              colors=torch.empty(n, dtype=torch.uint32, device="cuda"),
+                              counts=torch.empty(n, dtype=torch.uint32, device="cuda"),
+                              labels=torch.empty(n, dtype=torch.uint8, device="cuda"),
+                              index=torch.empty(img.shape[:2], dtype=torch.uint8,
+                                                device="cuda")))
+        nus = wsm.wsm_reduce_batch(h, batch)
+        assert nus[-3] == 1 and nus[-2] == 64 * 64
+        Ks = [min(256, 4 + 13 * q, nu) for q, nu in enumerate(nus)]
+        for im, K in zip(batch, Ks):
+            im["K"] = K
+            im["centers"] = torch.empty((K, 4), dtype=torch.float32, device="cuda")
+        wsm.wsm_init_batch(h, batch, seeds)
+        init_c = [im["centers"].clone() for im in batch]
+        init_l = [im["labels"][:nu].clone() for im, nu in zip(batch, nus)]
+        wsm.wsm_iterate_batch(h, batch, 3, 0.0)
+        wsm.wsm_map_batch(h, batch)
+        mse_b = wsm.wsm_distortion_batch(h, batch)
+        d_mse = torch.zeros(len(batch), dtype=torch.float64, device="cuda")
+        wsm.wsm_distortion_batch(h, batch, d_mse=d_mse, sync=False)
+        wsm.wsm_sync_status(h)
+        for q, (im, nu) in enumerate(zip(batch, nus)):
+            n = im["colors"].numel()
+            colors = torch.empty(n, dtype=torch.uint32, device="cuda")
+            counts = torch.empty(n, dtype=torch.uint32, device="cuda")
+            assert wsm.wsm_reduce(h, im["rgb"], colors, counts) == nu
+            assert torch.equal(colors[:nu], im["colors"][:nu])
+            assert torch.equal(counts[:nu], im["counts"][:nu])
+            centers = torch.empty_like(im["centers"])
+            labels = torch.full((nu,), 9, dtype=torch.uint8, device="cuda")
+            wsm.wsm_init(h, colors[:nu], nu, Ks[q], seeds[q], centers, labels)
+            assert torch.equal(centers, init_c[q])
+            assert torch.equal(labels, init_l[q])
+            m = wsm.wsm_distortion(h, im["rgb"], im["centers"], Ks[q], im["index"])
+            assert m == mse_b[q] == float(d_mse[q])
+    for q in (0, len(imgs) - 1):
+        ref_colors, ref_counts = oracle.unique(imgs[q])
+        assert np.array_equal(batch[q]["colors"][:nus[q]].cpu().numpy(), ref_colors)
+        assert np.array_equal(batch[q]["counts"][:nus[q]].cpu().numpy(), ref_counts)
+
+
+def test_quantize_batch_equals_quantize(wsm):
+    imgs = [synth.image(hh, ww, 40 + q, 3 + 4 * q) for q, (hh, ww) in
+            enumerate([(256, 256), (120, 200), (64, 48)])]
+    seeds = [5, 6, 7]
+    outs = wsm.quantize_batch([torch.from_numpy(i).cuda() for i in imgs], 32, seeds,
+                              max_iter=100, eps=1e-4)
+    for img, s, qb in zip(imgs, seeds, outs):
+        q1 = wsm.quantize(torch.from_numpy(img).cuda(), 32, s, max_iter=100, eps=1e-4)
+        assert q1.n_unique == qb.n_unique and q1.iters == qb.iters
+        assert torch.equal(q1.centers, qb.centers)
+        assert torch.equal(q1.index, qb.index)
+        assert torch.equal(q1.labels, qb.labels)
+        assert q1.mse == qb.mse
