@@ -66,6 +66,39 @@ def dist_env():
     return world, rank, local
 
 
+def combine_ranks(total_ms: float, e2e_ms: float, units: float, device):
+    """Whole-job figures of the replicas: the slowest rank's device and
+    end-to-end times (max over ranks) and the units all ranks processed
+    (sum).  Each rank quantizes its own images; this is the only exchange."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(u[0])
+
+
+def profiled_traffic():
+    """DRAM bytes (read + write) of one iterate launch from the committed ncu
+    summary, or None if the kernel sources changed since that capture."""
+    import hashlib
+    root = os.path.dirname(os.path.abspath(__file__))
+    csrc = os.path.join(root, "paper_1011_0093_gb300", "csrc")
+    try:
+        text = open(os.path.join(root, "profiles", "k_sortmeans_sweep8x512_K256.md")).read()
+        src = b"".join(open(os.path.join(csrc, f), "rb").read()
+                       for f in ("wsm_iterate.cu", "wsm_internal.cuh"))
+    except OSError:
+        return None
+    fields = dict(line.split(": ", 1) for line in text.splitlines()
+                  if line.startswith(("traffic_bytes_per_launch: ", "source_sha256: ")))
+    if fields.get("source_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+        return None
+    return int(fields["traffic_bytes_per_launch"])
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -311,13 +344,7 @@ def run_gpu(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
-    t_max = torch.tensor([total_ms, sum(e2e_ms)], dtype=torch.float64, device=dev)
-    units = torch.tensor([float(units_step)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        dist.all_reduce(units, op=dist.ReduceOp.SUM)
-    total_ms, e2e_total = float(t_max[0]), float(t_max[1])
-    all_units = float(units[0])
+    total_ms, e2e_total, all_units = combine_ranks(total_ms, sum(e2e_ms), units_step, dev)
     value = all_units * args.steps / (total_ms * 1e-3)
     e2e_value = all_units * args.steps / (e2e_total * 1e-3)
 
@@ -344,7 +371,7 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "alu", "kernel": "k_sortmeans<iterate> (8 images per launch)",
                          "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / fp32_peak, "traffic": None,
+                         "frac": achieved_tflops / fp32_peak, "traffic": profiled_traffic(),
                          "peak_kind": f"FP32 {sms} SMs x 128 x 2 x {pk.get('sm_max_mhz')} MHz "
                                       f"({pk_kind} max clock)",
                          "launch_ms": sum(it_ms) / len(it_ms),
