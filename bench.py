@@ -16,6 +16,9 @@ Workload (one step): 8 seeded 512x512 RGB images (noise amplitude swept
   cpu_baseline  the CPU oracle on a bounded sample of the same workload.
 
 ``--impl reference`` times the CPU oracle instead (the reference arm).
+``--form grad`` times the differentiable form instead: forward + backward of
+the weighted distortion D(C, X) of a 512x512 image's pixels at K = 64, and
+200 Adam steps of palette refinement from the WSM palette.
 Multi-GPU (torchrun): every rank quantizes its own 8 images (weak scaling,
 no collective on the data path); the step time is the max over ranks.
 """
@@ -386,12 +389,156 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_grad(args):
+    """Differentiable distortion, forward + backward (dD/dC and dD/dX) per step."""
+    import torch
+
+    import paper_1011_0093_gb300 as wsm
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    Kg = 64
+    img = synth.image(512, 512, 41, 6)
+    n = img.shape[0] * img.shape[1]
+    q = wsm.quantize(torch.from_numpy(img).to(dev), Kg, 5, max_iter=ITERS, eps=0.0)
+    C0 = q.centers[:, :3].contiguous()
+    x_host = torch.from_numpy(img.reshape(-1, 3).astype(np.float32)).pin_memory()
+    X = x_host.to(dev)
+    h = wsm.Handle(Kg, 1, 1)
+    assign = torch.empty(n, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step(X_in, C_in, warm):
+        Xg = X_in.detach().requires_grad_(True)
+        Cg = C_in.detach().requires_grad_(True)
+        D = wsm.weighted_distortion(Xg, Cg, assign=assign, warm_start=warm, handle=h)
+        D.backward()
+        return D, Cg.grad, Xg.grad
+
+    step(X, C0, False)
+    for _ in range(args.warmup):
+        step(X, C0, True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(X, C0, True)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    # the same through the public API from pinned host memory: the points go
+    # up, D and dD/dC come back every step
+    e2e = []
+    out_c = torch.empty((Kg, 3), dtype=torch.float32).pin_memory()
+    out_d = torch.empty(1, dtype=torch.float32).pin_memory()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Xd = x_host.to(dev, non_blocking=True)
+        D, gC, _ = step(Xd, C0, True)
+        out_c.copy_(gC, non_blocking=True)
+        out_d.copy_(D.detach().reshape(1), non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e.append(a.elapsed_time(b))
+    # per-kernel view: forward call (rows + search + sums) and backward kernel
+    fwd_ms, bwd_ms = [], []
+    D = torch.empty(1, dtype=torch.float32, device=dev)
+    resid = torch.empty((Kg, 4), dtype=torch.float32, device=dev)
+    gD = torch.ones(1, dtype=torch.float32, device=dev)
+    gC = torch.empty_like(C0)
+    gX = torch.empty_like(X)
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        wsm.wsm_distortion_fwd(h, X, None, C0, assign, True, D, resid)
+        e[1].record(stream)
+        wsm.wsm_distortion_bwd(h, X, None, C0, assign, resid, gD, gC, gX)
+        e[2].record(stream)
+        e[2].synchronize()
+        fwd_ms.append(e[0].elapsed_time(e[1]))
+        bwd_ms.append(e[1].elapsed_time(e[2]))
+    # 200 Adam steps from the WSM palette, assignment carried as warm start
+    Cp = C0.clone().requires_grad_(True)
+    opt = torch.optim.Adam([Cp], lr=0.1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d_start = None
+    for k in range(200):
+        opt.zero_grad()
+        Dk = wsm.weighted_distortion(X, Cp, assign=assign, warm_start=True, handle=h)
+        Dk.backward()
+        if d_start is None:
+            d_start = float(Dk.detach())
+        opt.step()
+    torch.cuda.synchronize()
+    adam_ms = (time.perf_counter() - t0) * 1e3
+    d_end = float(wsm.weighted_distortion(X, Cp.detach(), assign=assign, warm_start=True,
+                                          handle=h))
+    clk = clocks.stop()
+    wsm.wsm_sync_status(h)
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        Xd64 = img.reshape(-1, 3).astype(np.float64)
+        w64 = np.full(n, 1.0 / n)
+        C64 = C0.cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < min(args.cpu_seconds, 5.0) or reps == 0:
+            oracle.distortion_grad(Xd64, w64, C64)
+            reps += 1
+        secs = time.perf_counter() - t0
+        cpu = {"value": reps * n / secs, "unit": "points/s", "cores": 1, "kind": "oracle",
+               "sample": f"{reps} FP64 forward+gradient passes (exhaustive) over the same "
+                         f"{n} points, single thread, {secs:.1f} s"}
+    step_ms = statistics.median(ms)
+    bwd_bytes = n * (12 + 1 + 12)            # x read, assignment read, dD/dX written
+    pk, pk_kind = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    bwd_gbs = bwd_bytes / (statistics.median(bwd_ms) * 1e-3) / 1e9
+    line = {
+        "metric": "differentiable weighted distortion, forward + backward (dD/dC, dD/dX)",
+        "form": "grad", "value": n / (step_ms * 1e-3), "unit": "points/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "512x512 image (seed 41, noise 6) as float points, w_i = 1/N, "
+                               "K=64 palette from 10 WSM iterations, warm-started search",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "e2e": {"value": n / (statistics.median(e2e) * 1e-3), "unit": "points/s",
+                "h2d_bytes_per_step": n * 12, "d2h_bytes_per_step": Kg * 12 + 4},
+        "kernels_ms": {"forward_call": statistics.median(fwd_ms),
+                       "backward_call": statistics.median(bwd_ms)},
+        "roofline": {"bound": "hbm", "kernel": "k_grad_bwd", "achieved": bwd_gbs, "peak": hbm,
+                     "unit": "GB/s", "frac": bwd_gbs / hbm, "traffic": None,
+                     "peak_kind": pk_kind, "bytes_per_launch": bwd_bytes},
+        "adam": {"steps": 200, "lr": 0.1, "ms": adam_ms, "D_start": d_start, "D_end": d_end},
+        "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": 4 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wsm", choices=["wsm", "reference"])
+    ap.add_argument("--form", default="plain", choices=["plain", "grad"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -399,6 +546,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.form == "grad":
+        run_grad(args)
     else:
         run_gpu(args)
 

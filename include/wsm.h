@@ -289,6 +289,43 @@ WSM_API int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels
                    const float* d_centers, int K, const uint8_t* d_index, double* d_mse,
                    double* mse, wsm_stream stream);
 
+/* The weighted distortion of Eq. 1 (the k-means objective) with the sample
+ * weights of Sec. 2, as a differentiable function of the palette C and of
+ * the points X:  D(C, X) = sum_i w_i min_k ||x_i - c_k||^2.  Forward pass:
+ * each point's nearest center m_i by the pruned search of Algorithm 2
+ * (Sec. 2), starting at d_assign[i] if warm_start (else at center 0), over
+ * full sorted rows of C; among equal distances the center visited last wins.
+ *   d_x       device float [n][x_stride] (x_stride 3 or 4; a 4th value is ignored)
+ *   d_w       device float [n] weights, or NULL for w_i = 1/n
+ *   d_centers device float [K][c_stride] (c_stride 3 or 4), 1 <= K <= max_K
+ *   d_assign  device uint8 [n]: in, the starting centers (if warm_start,
+ *             each < K); out, m_i
+ *   d_D       device float [1]: D
+ *   d_resid   device float [K][4], 16-byte aligned: (R_k, W_k) with
+ *             R_k = sum_{m_i = k} w_i (x_i - c_k), W_k = sum_{m_i = k} w_i;
+ *             the input of wsm_distortion_bwd
+ * All sums are FP32 in a fixed order (identical results run to run).  n may
+ * be 0 (D = 0).  Asynchronous.  Uses the handle's gradient scratch: calls on
+ * one handle must be ordered on one stream.
+ * Errors: WSM_E_INVAL (strides, K, n > 2^31, pointers; a starting center
+ * >= K is reported at the next synchronising call). */
+WSM_API int wsm_distortion_fwd(wsm_handle* h, const float* d_x, int x_stride, const float* d_w,
+                               int64_t n, const float* d_centers, int c_stride, int K,
+                               uint8_t* d_assign, int warm_start, float* d_D, float* d_resid,
+                               wsm_stream stream);
+
+/* Backward pass of wsm_distortion_fwd for the upstream gradient g = *d_gD
+ * (device float [1]), away from ties (where D is differentiable):
+ *   d_gC  device float [K][c_stride] (may be NULL): -2 g R_k (0 in a 4th column)
+ *   d_gX  device float [n][x_stride] (may be NULL): 2 g w_i (x_i - c_{m_i})
+ * with d_assign and d_resid from the forward pass on the same d_x, d_w and
+ * d_centers.  Asynchronous.
+ * Errors: as wsm_distortion_fwd. */
+WSM_API int wsm_distortion_bwd(wsm_handle* h, const float* d_x, int x_stride, const float* d_w,
+                               int64_t n, const float* d_centers, int c_stride, int K,
+                               const uint8_t* d_assign, const float* d_resid, const float* d_gD,
+                               float* d_gC, float* d_gX, wsm_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,10 @@ SIGNATURES = {
     "wsm_reduce_batch": (C.c_int, [_P, _P, C.c_int, _P]),
     "wsm_init_batch": (C.c_int, [_P, _P, C.c_int, _P, _P]),
     "wsm_distortion_batch": (C.c_int, [_P, _P, C.c_int, _P, _P, _P]),
+    "wsm_distortion_fwd": (C.c_int, [_P, _P, C.c_int, _P, _I64, _P, C.c_int, C.c_int, _P,
+                                     C.c_int, _P, _P, _P]),
+    "wsm_distortion_bwd": (C.c_int, [_P, _P, C.c_int, _P, _I64, _P, C.c_int, C.c_int, _P, _P,
+                                     _P, _P, _P, _P]),
     "wsm_distortion": (C.c_int, [_P, _P, _I64, C.c_int, _P, C.c_int, _P, _P,
                                  C.POINTER(C.c_double), _P]),
 }
@@ -348,3 +352,43 @@ def wsm_distortion(h: Handle, rgb: torch.Tensor, centers: torch.Tensor, K: int,
                                 _dev(d_mse, torch.float64, "d_mse", 1),
                                 C.byref(m) if sync else None, _stream(stream)))
     return m.value if sync else None
+
+
+def _points(t: torch.Tensor, name: str) -> tuple[int, int]:
+    if t.dim() != 2 or t.shape[1] not in (3, 4):
+        raise ValueError(f"{name} must be float32 [n, 3|4]")
+    return t.shape[0], t.shape[1]
+
+
+def wsm_distortion_fwd(h: Handle, x: torch.Tensor, w: torch.Tensor | None, centers: torch.Tensor,
+                       assign: torch.Tensor, warm_start: bool, D: torch.Tensor,
+                       resid: torch.Tensor, stream=None):
+    """Forward pass of the weighted distortion: fills D [1], resid [K, 4] and assign [n]."""
+    n, xs = _points(x, "x")
+    K, cs = _points(centers, "centers")
+    _check(lib().wsm_distortion_fwd(h.ptr, _dev(x, torch.float32, "x"), xs,
+                                    _dev(w, torch.float32, "w", n), n,
+                                    _dev(centers, torch.float32, "centers"), cs, K,
+                                    _dev(assign, torch.uint8, "assign", n), int(bool(warm_start)),
+                                    _dev(D, torch.float32, "D", 1),
+                                    _dev(resid, torch.float32, "resid", 4 * K), _stream(stream)))
+
+
+def wsm_distortion_bwd(h: Handle, x: torch.Tensor, w: torch.Tensor | None, centers: torch.Tensor,
+                       assign: torch.Tensor, resid: torch.Tensor, gD: torch.Tensor,
+                       gC: torch.Tensor | None, gX: torch.Tensor | None, stream=None):
+    """Backward pass: fills gC [K, 3|4] and gX [n, 3|4] (either may be None)."""
+    n, xs = _points(x, "x")
+    K, cs = _points(centers, "centers")
+    if gC is not None and tuple(gC.shape) != (K, cs):
+        raise ValueError("gC must have the shape of centers")
+    if gX is not None and tuple(gX.shape) != (n, xs):
+        raise ValueError("gX must have the shape of x")
+    _check(lib().wsm_distortion_bwd(h.ptr, _dev(x, torch.float32, "x"), xs,
+                                    _dev(w, torch.float32, "w", n), n,
+                                    _dev(centers, torch.float32, "centers"), cs, K,
+                                    _dev(assign, torch.uint8, "assign", n),
+                                    _dev(resid, torch.float32, "resid", 4 * K),
+                                    _dev(gD, torch.float32, "gD", 1),
+                                    _dev(gC, torch.float32, "gC"), _dev(gX, torch.float32, "gX"),
+                                    _stream(stream)))

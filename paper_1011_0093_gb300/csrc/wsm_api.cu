@@ -252,6 +252,9 @@ extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64
     } allocs[] = {
         {(void**)&h->mse_part, sizeof(double) * 1032},   // 1024 partials + result
         {(void**)&h->ctrl, sizeof(Ctrl)},
+        {(void**)&h->grad_tab, sizeof(float4) * (size_t)max_K * max_K},
+        {(void**)&h->grad_nb, (size_t)max_K * max_K},
+        {(void**)&h->grad_part, sizeof(float4) * (size_t)grad_blocks(h) * (max_K + 1)},
     };
     for (auto& a : allocs) {
         e = cudaMalloc(a.p, a.bytes);
@@ -288,7 +291,7 @@ extern "C" int wsm_destroy(wsm_handle* h) {
     if (h->device >= 0 && prev != h->device) cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     free_slots(h);
-    void* dev_ptrs[] = {h->mse_part, h->ctrl};
+    void* dev_ptrs[] = {h->mse_part, h->ctrl, h->grad_tab, h->grad_nb, h->grad_part};
     for (void* p : dev_ptrs)
         if (p) cudaFree(p);
     if (h->host_ctrl) cudaFreeHost(h->host_ctrl);

@@ -142,59 +142,6 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
-// Row-sort key of center t in row p: the bits of d (>= 0, so they order like
-// the values) above the tie order (t != p, t).
-__device__ __forceinline__ unsigned long long row_key(float d, int t, int p) {
-    return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(t == p ? 0 : t + 1);
-}
-
-// The rows p = b, b + G, ... of one image's table, one row per warp at a time.
-// Row p keeps the centers t with d[p][t] < thr[p] (p itself always); the
-// rank of a key among the kept keys (keys are distinct) is its entry
-// position.  Four entries with an infinite bound follow the kept ones.
-__device__ __forceinline__ void build_rows(int K, int G, int b, const float4* s_c,
-                                           const float* s_thr, unsigned long long* s_wkey,
-                                           float4* tab, uint8_t* tab_nb) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, WPB = blockDim.x >> 5;
-    unsigned long long* key = s_wkey + (size_t)wid * K;        // this warp's buffer
-    const unsigned below = (1u << lane) - 1u;
-    for (int p = b + wid * G; p < K; p += G * WPB) {
-        const float4 cp = s_c[p];
-        const float bound = s_thr[p];
-        int L = 0;
-        for (int t0 = 0; t0 < K; t0 += 32) {
-            const int t = t0 + lane;
-            float d = 0.f;
-            bool keep = false;
-            if (t < K) {
-                const float4 ct = s_c[t];
-                d = sq3(cp.x, cp.y, cp.z, ct.x, ct.y, ct.z);
-                keep = d < bound || t == p;
-            }
-            const unsigned vote = __ballot_sync(0xFFFFFFFFu, keep);
-            if (keep) key[L + __popc(vote & below)] = row_key(d, t, p);
-            L += __popc(vote);
-        }
-        __syncwarp();
-        float4* row = tab + (size_t)p * K;
-        uint8_t* row_nb = tab_nb + (size_t)p * K;
-        for (int j = lane; j < L; j += 32) {
-            const unsigned long long kj = key[j];
-            int rank = 0;
-#pragma unroll 8
-            for (int k = 0; k < L; ++k) rank += key[k] < kj;
-            const unsigned lo = (unsigned)kj;
-            const int c = lo ? (int)lo - 1 : p;
-            const float4 ct = s_c[c];
-            row[rank] = make_float4(__uint_as_float((unsigned)(kj >> 32)) * 0.25f, ct.x, ct.y, ct.z);
-            row_nb[rank] = (uint8_t)c;
-        }
-        if (lane < 4 && L + lane < K)
-            row[L + lane] = make_float4(__int_as_float(0x7f800000), 0.f, 0.f, 0.f);
-        __syncwarp();
-    }
-}
-
 // One visited entry: distance, and the update with the later entry winning ties.
 #define WSM_VISIT(e, jj)                                        \
     {                                                           \
