@@ -289,6 +289,55 @@ WSM_API int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels
                    const float* d_centers, int K, const uint8_t* d_index, double* d_mse,
                    double* mse, wsm_stream stream);
 
+/* The whole path -- Sec. 2 unique colors, Algorithm 2 (initialisation,
+ * Sort-Means iterations with the Sec. 3.2 stop rule), Sec. 1 final
+ * assignment and pixel mapping, Eq. 2 MSE -- for n_items images, with no
+ * host synchronisation: N' of each image stays on the device (the
+ * initialisation draws its Floyd sample there, the persistent launches split
+ * their blocks there).  The call only enqueues work, so it can be captured
+ * into a CUDA graph (cudaStreamBeginCapture on `stream`) and replayed.
+ * Results equal those of wsm_reduce, wsm_init(seeds[i]), wsm_iterate,
+ * wsm_map and wsm_distortion image by image, bit for bit.
+ * Each item needs d_rgb, n_pixels, pixel_stride, K and device buffers with
+ * room for n_pixels entries in d_colors, d_counts and d_labels, [K][4]
+ * d_centers and [n_pixels] d_index; n_unique is not read.
+ *   seeds       host uint64 [n_items]
+ *   d_n_unique  device int64 [n_items] (may be NULL): N'
+ *   d_iters     device int [n_items] (may be NULL): iterations run
+ *   d_mse       device double [n_items] (may be NULL): MSE
+ * An image with N' < K is skipped and reported (WSM_E_INVAL) at the next
+ * synchronising call, e.g. wsm_sync_status.
+ * Errors: WSM_E_INVAL (sizes, pointers, more items than reserved slots). */
+WSM_API int wsm_quantize_batch(wsm_handle* h, const wsm_item* items, int n_items,
+                               const uint64_t* seeds, int max_iter, double eps,
+                               int64_t* d_n_unique, int* d_iters, double* d_mse,
+                               wsm_stream stream);
+
+/* Launch shapes of the persistent Sort-Means kernel (no counterpart in the
+ * paper: a GPU launch parameter).  Shape s = (threads per block, blocks per
+ * SM); the persistent launches of the handle use its current shape.  Every
+ * shape gives the same results bit for bit.
+ * wsm_launch_shape: shape s (or, for s < 0, the current one) -> *threads,
+ * *blocks_per_sm, *resident (1 if all its blocks fit on the GPU at this
+ * handle's max_K); returns s (>= 0) or an error code.
+ * wsm_set_launch_shape: makes s current.  Errors: WSM_E_INVAL (out of range,
+ * not resident). */
+WSM_API int wsm_launch_shape(wsm_handle* h, int shape, int* threads, int* blocks_per_sm,
+                             int* resident);
+WSM_API int wsm_set_launch_shape(wsm_handle* h, int shape);
+
+/* Autotuner: runs the unique-color reduction of the batch once, then for
+ * every resident shape `repeats` times the initialisation (untimed) and the
+ * Sort-Means iterations (timed with CUDA events on `stream`), and makes the
+ * fastest shape current.  Synchronises.  Items as for wsm_quantize_batch;
+ * their centers and labels end as one complete run leaves them.
+ *   times_ms  host float [5] (may be NULL): best time of each shape, -1 if
+ *             not resident
+ * Returns the chosen shape (>= 0) or an error code. */
+WSM_API int wsm_autotune_batch(wsm_handle* h, const wsm_item* items, int n_items,
+                               const uint64_t* seeds, int max_iter, double eps, int repeats,
+                               float* times_ms, wsm_stream stream);
+
 /* The weighted distortion of Eq. 1 (the k-means objective) with the sample
  * weights of Sec. 2, as a differentiable function of the palette C and of
  * the points X:  D(C, X) = sum_i w_i min_k ||x_i - c_k||^2.  Forward pass:

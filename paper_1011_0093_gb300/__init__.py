@@ -4,15 +4,19 @@ Implements the method of M. E. Celebi, "Fast Color Quantization Using
 Weighted Sort-Means Clustering" (arXiv:1011.0093) as hand-written CUDA for
 sm_103a behind the C ABI of include/wsm.h (libwsm.so).  This package is the
 thin Python layer above it: ``_native`` marshals arguments to the C entry
-points, ``quantize`` chains them for one image or a batch, ``distortion`` wraps
-the weighted distortion and its gradients as a torch.autograd.Function.  PyTorch only provides device
-memory and streams.
+points; ``quantize`` chains them for one image or a batch; ``batch`` holds a
+fixed batch's buffers and captures the whole path into a CUDA graph;
+``distortion`` wraps the weighted distortion and its gradients as a
+torch.autograd.Function.  PyTorch only provides device memory and streams.
 """
 from ._native import (MAX_K, MAX_PIXELS, Handle, WsmError, lib, wsm_distortion,
-                      wsm_distortion_batch, wsm_distortion_bwd, wsm_distortion_fwd, wsm_init, wsm_init_batch, wsm_iterate,
+                      wsm_distortion_batch, wsm_distortion_bwd, wsm_distortion_fwd, wsm_init,
+                      wsm_init_batch, wsm_iterate,
                       wsm_iterate_batch, wsm_iterate_noalloc, wsm_iterate_stats, wsm_map,
                       wsm_map_batch, wsm_reduce, wsm_reduce_batch, wsm_reserve_batch,
-                      wsm_sync_status)
+                      wsm_sync_status, wsm_quantize_batch, wsm_autotune_batch,
+                      wsm_launch_shape, wsm_set_launch_shape, pipeline_items)
+from .batch import BatchPlan
 from .distortion import WeightedDistortion, weighted_distortion
 from .quantize import Quantized, quantize, quantize_batch
 
@@ -20,5 +24,7 @@ __all__ = ["MAX_K", "MAX_PIXELS", "Handle", "WsmError", "lib", "wsm_reduce", "ws
            "wsm_iterate", "wsm_iterate_noalloc", "wsm_iterate_stats", "wsm_iterate_batch",
            "wsm_map_batch", "wsm_reserve_batch", "wsm_reduce_batch", "wsm_init_batch",
            "wsm_distortion_batch", "wsm_distortion_fwd", "wsm_distortion_bwd",
-           "WeightedDistortion", "weighted_distortion", "wsm_map", "wsm_distortion", "wsm_sync_status",
+           "WeightedDistortion", "weighted_distortion", "wsm_quantize_batch",
+           "wsm_autotune_batch", "wsm_launch_shape", "wsm_set_launch_shape", "pipeline_items",
+           "BatchPlan", "wsm_map", "wsm_distortion", "wsm_sync_status",
            "Quantized", "quantize", "quantize_batch"]

@@ -55,6 +55,11 @@ SIGNATURES = {
     "wsm_reduce_batch": (C.c_int, [_P, _P, C.c_int, _P]),
     "wsm_init_batch": (C.c_int, [_P, _P, C.c_int, _P, _P]),
     "wsm_distortion_batch": (C.c_int, [_P, _P, C.c_int, _P, _P, _P]),
+    "wsm_quantize_batch": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_double, _P, _P, _P, _P]),
+    "wsm_launch_shape": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int)]),
+    "wsm_set_launch_shape": (C.c_int, [_P, C.c_int]),
+    "wsm_autotune_batch": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_double, C.c_int, _P, _P]),
     "wsm_distortion_fwd": (C.c_int, [_P, _P, C.c_int, _P, _I64, _P, C.c_int, C.c_int, _P,
                                      C.c_int, _P, _P, _P]),
     "wsm_distortion_bwd": (C.c_int, [_P, _P, C.c_int, _P, _I64, _P, C.c_int, C.c_int, _P, _P,
@@ -86,6 +91,13 @@ def lib():
                 f.argtypes = args
             _lib = so
     return _lib
+
+
+def _check_index(rc: int) -> int:
+    """For calls that return an index >= 0 or a negative error code."""
+    if rc < 0:
+        _check(rc)
+    return rc
 
 
 def _check(rc: int):
@@ -392,3 +404,73 @@ def wsm_distortion_bwd(h: Handle, x: torch.Tensor, w: torch.Tensor | None, cente
                                     _dev(gD, torch.float32, "gD", 1),
                                     _dev(gC, torch.float32, "gC"), _dev(gX, torch.float32, "gX"),
                                     _stream(stream)))
+
+
+N_SHAPES = 5
+
+
+def pipeline_items(images: list[dict]):
+    """Marshal dicts with rgb, K, colors, counts, centers, labels, index (device
+    buffers of wsm_quantize_batch) into a wsm_item array; the array keeps the
+    pointers, so it can be reused for as long as the tensors live."""
+    arr = (WsmItem * max(len(images), 1))()
+    for q, im in enumerate(images):
+        n, stride = _pixels(im["rgb"])
+        K = int(im["K"])
+        it = arr[q]
+        it.d_rgb = _dev(im["rgb"], torch.uint8, "rgb")
+        it.n_pixels = n
+        it.pixel_stride = stride
+        it.K = K
+        it.d_colors = _dev(im["colors"], torch.uint32, "colors", n)
+        it.d_counts = _dev(im["counts"], torch.uint32, "counts", n)
+        it.n_unique = 0
+        it.d_centers = _dev(im["centers"], torch.float32, "centers", 4 * K)
+        it.d_labels = _dev(im["labels"], torch.uint8, "labels", n)
+        it.d_index = _dev(im["index"], torch.uint8, "index", n)
+    return arr
+
+
+def _seeds(seeds, n):
+    if len(seeds) != n:
+        raise ValueError("one seed per image")
+    return (C.c_uint64 * max(n, 1))(*[int(x) & (2**64 - 1) for x in seeds])
+
+
+def wsm_quantize_batch(h: Handle, items, n_items: int, seeds, max_iter: int, eps: float,
+                       d_n_unique: torch.Tensor | None = None, d_iters: torch.Tensor | None = None,
+                       d_mse: torch.Tensor | None = None, stream=None):
+    """Enqueue the whole path for a batch (items: a pipeline_items array);
+    nothing is synchronised, so a CUDA graph can capture it."""
+    sd = seeds if isinstance(seeds, C.Array) else _seeds(seeds, n_items)
+    _check(lib().wsm_quantize_batch(h.ptr, C.cast(items, C.c_void_p), n_items,
+                                    C.cast(sd, C.c_void_p), int(max_iter), float(eps),
+                                    _dev(d_n_unique, torch.int64, "d_n_unique", n_items),
+                                    _dev(d_iters, torch.int32, "d_iters", n_items),
+                                    _dev(d_mse, torch.float64, "d_mse", n_items),
+                                    _stream(stream)))
+
+
+def wsm_launch_shape(h: Handle, shape: int = -1) -> tuple[int, int, int, bool]:
+    """(shape, threads per block, blocks per SM, resident) of a launch shape."""
+    t, b, r = C.c_int(0), C.c_int(0), C.c_int(0)
+    q = _check_index(lib().wsm_launch_shape(h.ptr, int(shape), C.byref(t), C.byref(b),
+                                            C.byref(r)))
+    return q, t.value, b.value, bool(r.value)
+
+
+def wsm_set_launch_shape(h: Handle, shape: int):
+    _check(lib().wsm_set_launch_shape(h.ptr, int(shape)))
+
+
+def wsm_autotune_batch(h: Handle, items, n_items: int, seeds, max_iter: int, eps: float,
+                       repeats: int = 2, stream=None) -> tuple[int, list[float]]:
+    """Time every resident launch shape on the batch; keeps and returns the
+    fastest, with each shape's best time in ms (-1: not resident)."""
+    sd = seeds if isinstance(seeds, C.Array) else _seeds(seeds, n_items)
+    times = (C.c_float * N_SHAPES)()
+    q = _check_index(lib().wsm_autotune_batch(h.ptr, C.cast(items, C.c_void_p), n_items,
+                                              C.cast(sd, C.c_void_p), int(max_iter), float(eps),
+                                              int(repeats), C.cast(times, C.c_void_p),
+                                              _stream(stream)))
+    return q, [times[i] for i in range(N_SHAPES)]

@@ -46,13 +46,15 @@ int read_status(wsm_handle* h, cudaStream_t s) {
     if (st & ST_TIMEOUT) return fail(WSM_E_TIMEOUT, "a device-side grid barrier timed out");
     if (st & ST_CAPACITY)
         return fail(WSM_E_CAPACITY, "more unique colors than the output capacity");
+    if (st & ST_FEW_COLORS)
+        return fail(WSM_E_INVAL, "an image has fewer unique colors than K (it was skipped)");
     if (st & ST_BAD_LABEL) return fail(WSM_E_INVAL, "a membership or palette index was >= K");
     return WSM_OK;
 }
 
 // splitmix64 (Steele, Lea, Flood 2014): draw r of the stream seeded with
 // `seed` is the state seed + (r+1) * golden-gamma passed through the mixer.
-static uint64_t splitmix_draw(uint64_t seed, uint64_t r) {
+__host__ __device__ static inline uint64_t splitmix_draw(uint64_t seed, uint64_t r) {
     uint64_t s = seed + 0x9E3779B97F4A7C15ull * (r + 1ull);
     s ^= s >> 30;
     s *= 0xBF58476D1CE4E5B9ull;
@@ -120,12 +122,96 @@ __global__ void k_init_batch(const __grid_constant__ InitItems B) {
     for (int64_t q = tid; q < B.n_unique[i]; q += (int64_t)G * blockDim.x) B.labels[i][q] = 0;
 }
 
+// The initialisation of a batch whose N' values are on the device (written
+// by the reduction): image i owns blocks [i * kInitBlocks, (i+1) * kInitBlocks)
+// which zero its labels; the first of them also draws the K indices exactly
+// as floyd_sample does on the host (the splitmix64 draws in parallel, the
+// Floyd steps in order with a warp checking the earlier picks), sorts them
+// and gathers the centers.  An image with N' < K gets ST_FEW_COLORS.
+constexpr int kInitBlocks = 8;
+
+struct InitDevItems {
+    int n_items;
+    const int64_t* n_dev;           // N' of item i at n_dev[i]
+    const uint32_t* colors[kMaxBatch];
+    int K[kMaxBatch];
+    float4* centers[kMaxBatch];
+    uint8_t* labels[kMaxBatch];
+    uint64_t seed[kMaxBatch];
+    unsigned* status;
+};
+
+__global__ void __launch_bounds__(256) k_init_dev(const __grid_constant__ InitDevItems B) {
+    __shared__ uint64_t s_draw[WSM_MAX_K];
+    __shared__ uint32_t s_pick[WSM_MAX_K];
+    __shared__ uint32_t s_sorted[WSM_MAX_K];
+    const int i = blockIdx.x / kInitBlocks, j = blockIdx.x % kInitBlocks;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t n = B.n_dev[i];
+    const int K = B.K[i];
+    if (n < K) {
+        if (j == 0 && tid == 0) atomicOr(B.status, ST_FEW_COLORS);
+        return;
+    }
+    for (int64_t q = (int64_t)j * blockDim.x + tid; q < n; q += (int64_t)kInitBlocks * blockDim.x)
+        B.labels[i][q] = 0;
+    if (j != 0) return;
+    for (int r = tid; r < K; r += blockDim.x)
+        s_draw[r] = splitmix_draw(B.seed[i], (uint64_t)r) % (uint64_t)(n - K + r + 1);
+    __syncthreads();
+    if (tid < 32) {
+        for (int r = 0; r < K; ++r) {
+            const uint32_t t = (uint32_t)s_draw[r];
+            bool seen = false;
+            for (int q = lane; q < r; q += 32) seen |= s_pick[q] == t;
+            seen = __any_sync(0xFFFFFFFFu, seen);
+            if (lane == 0) s_pick[r] = seen ? (uint32_t)(n - K + r) : t;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int r = tid; r < K; r += blockDim.x) {     // the picks are distinct: rank = position
+        const uint32_t v = s_pick[r];
+        int rank = 0;
+        for (int q = 0; q < K; ++q) rank += s_pick[q] < v;
+        s_sorted[rank] = v;
+    }
+    __syncthreads();
+    for (int k = tid; k < K; k += blockDim.x) {
+        const uint32_t c = B.colors[i][s_sorted[k]];
+        B.centers[i][k] = make_float4((float)((c >> 16) & 255u), (float)((c >> 8) & 255u),
+                                      (float)(c & 255u), 0.f);
+    }
+}
+
+int init_items_dev(wsm_handle* h, const wsm_item* items, int n_items, const uint64_t* seeds,
+                   cudaStream_t s) {
+    for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
+        InitDevItems B;
+        B.n_items = std::min(kMaxBatch, n_items - i0);
+        B.n_dev = h->batch_nu + i0;
+        B.status = &h->ctrl->status;
+        for (int q = 0; q < B.n_items; ++q) {
+            const wsm_item& it = items[i0 + q];
+            B.colors[q] = it.d_colors;
+            B.K[q] = it.K;
+            B.centers[q] = reinterpret_cast<float4*>(it.d_centers);
+            B.labels[q] = it.d_labels;
+            B.seed[q] = seeds[i0 + q];
+        }
+        k_init_dev<<<B.n_items * kInitBlocks, 256, 0, s>>>(B);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "init launch");
+    }
+    return WSM_OK;
+}
+
 int iterate_kernel_setup(wsm_handle* h);   // wsm_iterate.cu
 
 void free_slots(wsm_handle* h) {
     void* ptrs[] = {h->tab,   h->tab_nb, h->sums,      h->sums64,   h->acc,       h->trace,
                     h->lut,   h->slot_ctrl, h->hist,   h->bitmap,   h->blk_total, h->batch_nu,
-                    h->batch_mse, h->pick};
+                    h->batch_mse, h->pick, h->plan};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     void* host_ptrs[] = {h->host_nu, h->host_mse, h->host_pick};
@@ -137,6 +223,7 @@ void free_slots(wsm_handle* h) {
     h->batch_nu = nullptr;
     h->batch_mse = nullptr;
     h->pick = nullptr;
+    h->plan = nullptr;
     h->host_nu = nullptr;
     h->host_mse = nullptr;
     h->host_pick = nullptr;
@@ -176,6 +263,7 @@ int alloc_slots(wsm_handle* h, int slots) {
         {(void**)&h->batch_nu, sizeof(int64_t) * n},
         {(void**)&h->batch_mse, sizeof(double) * n},
         {(void**)&h->pick, sizeof(uint32_t) * (size_t)h->max_K * n},
+        {(void**)&h->plan, sizeof(int) * (n / kMaxBatch + 1) * (kMaxBatch + 1)},
     };
     for (auto& a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.bytes);

@@ -17,6 +17,7 @@ enum : unsigned {
     ST_TIMEOUT = 1u,    // a grid barrier wait ran past its limit
     ST_BAD_LABEL = 2u,  // an input membership or palette index was >= K
     ST_CAPACITY = 4u,   // more unique colors than the output capacity
+    ST_FEW_COLORS = 8u, // an image of a device-sized batch has fewer unique colors than K
 };
 
 // A grid barrier waits at most this long (globaltimer ns) before giving up.
@@ -28,12 +29,19 @@ constexpr int kScanWordsPerThread = 4;       // bitmap words per thread in the c
 constexpr int kScanThreads = 512;
 constexpr int kScanWordsPerBlock = kScanWordsPerThread * kScanThreads;   // 2048
 constexpr int kScanBlocks = kMapWords / kScanWordsPerBlock;             // 256
-constexpr int kIterThreads = 512;            // threads per block of the persistent kernel
 constexpr int kMaxTrace = 4096;              // SSE values kept per wsm_iterate call
 constexpr int kCopies = 8;                   // replicas of the global accumulators
 constexpr int kChunk = 32;                   // colors per warp chunk (one per lane)
 constexpr int kMaxBatch = 48;                // images per persistent launch
 constexpr int kReduceSlots = 16;             // images per unique-color reduction launch
+
+// A launch shape of the persistent sort-means kernel.
+struct IterShape {
+    int threads;         // per block: 256, 512 or 1024
+    int blocks_per_sm;   // co-resident blocks per SM
+};
+constexpr int kNumIterShapes = 5;
+extern const IterShape kIterShapes[kNumIterShapes];
 
 // Control words in device memory (one block per handle).
 // The fields before `status` are cleared before every persistent launch, so
@@ -58,8 +66,8 @@ struct wsm_handle {
     int max_K = 0;
     int64_t max_pixels = 0;
     int64_t max_unique = 0;
-    int iter_grid = 0;           // co-resident blocks of the persistent kernel
-    int iter_blocks_per_sm = 0;
+    int iter_shape = 0;          // index into kIterShapes used by the persistent launches
+    bool shape_ok[wsm::kNumIterShapes] = {};   // shapes whose blocks can all be resident
     // scratch (device)
     double* mse_part = nullptr;  // [1024] block partials + [1] result
     wsm::Ctrl* ctrl = nullptr;   // status word, N', MSE mirror
@@ -87,6 +95,7 @@ struct wsm_handle {
     int64_t* batch_nu = nullptr;     // [slots] N' of each image of the last wsm_reduce_batch
     double* batch_mse = nullptr;     // [slots] MSE of each image of the last wsm_distortion_batch
     uint32_t* pick = nullptr;        // [slots][max_K] initial center indices (wsm_init_batch)
+    int* plan = nullptr;             // [slots / kMaxBatch + 1][kMaxBatch + 1] device-side block splits
     int64_t* host_nu = nullptr;      // pinned mirrors of the three arrays above
     double* host_mse = nullptr;
     uint32_t* host_pick = nullptr;
@@ -101,6 +110,27 @@ int check_handle(wsm_handle* h);
 int read_status(wsm_handle* h, cudaStream_t s);
 int alloc_slots(wsm_handle* h, int slots);
 int grad_blocks(wsm_handle* h);
+int iter_grid(const wsm_handle* h);
+
+// Stream-ordered pieces of the batch calls (no checks, no synchronisation);
+// item i of a call uses image slot i.  With n_dev, N' of item i is read on
+// the device from n_dev[i] (written by reduce_items into batch_nu).
+int check_item(wsm_handle* h, const wsm_item& it, bool need_pixels, bool need_counts);
+int check_pixels(wsm_handle* h, const wsm_item& it);
+int reduce_items(wsm_handle* h, const wsm_item* items, int n_items, cudaStream_t s);
+int init_items_dev(wsm_handle* h, const wsm_item* items, int n_items, const uint64_t* seeds,
+                   cudaStream_t s);
+int iterate_items(wsm_handle* h, const wsm_item* items, int n_items, int max_iter, double eps,
+                  const int64_t* n_dev, cudaStream_t s);
+int launch_sortmeans(wsm_handle* h, bool map_mode, const uint32_t* colors, const uint32_t* counts,
+                     int64_t n, int K, float* centers, uint8_t* labels, int max_iter, double eps,
+                     cudaStream_t s);
+int launch_map_items(wsm_handle* h, const wsm_item* items, int n_items, int slot0,
+                     const int64_t* n_dev, cudaStream_t s);
+int map_items(wsm_handle* h, const wsm_item* items, int n_items, const int64_t* n_dev,
+              cudaStream_t s);
+int distortion_items(wsm_handle* h, const wsm_item* items, int n_items, double* d_mse,
+                     cudaStream_t s);
 void free_slots(wsm_handle* h);
 
 // ---------------------------------------------------------------------------

@@ -81,9 +81,50 @@ struct BatchParams {
     int n_items;
     int max_iter;
     double eps;
+    const int64_t* n_dev;      // if set, image i has n_dev[item[i].slot] colors (written by an
+                               //   earlier kernel) and the split is first_dev (k_plan)
+    const int* first_dev;
     int first_blk[kMaxBatch + 1];  // image i owns blocks [first_blk[i], first_blk[i+1])
     ItemDesc item[kMaxBatch];
 };
+
+// Blocks of one image's group: enough for every lane to hold a color and for
+// every warp to hold a table row.
+__host__ __device__ inline int64_t group_want(int64_t n, int K, int threads) {
+    const int64_t warps = threads / 32;
+    const int64_t for_colors = (n + threads - 1) / threads;
+    const int64_t for_rows = (K + warps - 1) / warps;
+    const int64_t w = for_colors > for_rows ? for_colors : for_rows;
+    return w > 1 ? w : 1;
+}
+
+// Split `grid` blocks into one group per image, in proportion to each image's
+// want beyond its first block (every image gets at least one; grid >= n_items),
+// integer arithmetic only so that host and device derive the same split.
+// Returns the number of blocks used.
+__host__ __device__ inline int split_groups(const int64_t* want, int n_items, int grid,
+                                            int* first_blk) {
+    int64_t total = 0;
+    for (int i = 0; i < n_items; ++i) total += want[i];
+    first_blk[0] = 0;
+    if (total <= grid) {
+        for (int i = 0; i < n_items; ++i) first_blk[i + 1] = first_blk[i] + (int)want[i];
+        return first_blk[n_items];
+    }
+    const int64_t left = grid - n_items, excess = total - n_items;
+    int used = 0;
+    for (int i = 0; i < n_items; ++i) {
+        first_blk[i + 1] = 1 + (int)(left * (want[i] - 1) / excess);   // g_i, for now
+        used += first_blk[i + 1];
+    }
+    for (int i = 0; i < n_items && used < grid; ++i)   // the rounding remainder, in order
+        if (first_blk[i + 1] < want[i]) {
+            ++first_blk[i + 1];
+            ++used;
+        }
+    for (int i = 0; i < n_items; ++i) first_blk[i + 1] += first_blk[i];
+    return first_blk[n_items];
+}
 
 // floor(t / W) for t < 128 W (or t < 2^32 with a quotient below 2^8) and
 // 1 <= W <= 2^24: an FP32 estimate from the reciprocal, off by at most one,
@@ -142,6 +183,17 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
+// The block split of a launch whose image sizes are on the device, written
+// to first_dev before the persistent kernel starts.
+__global__ void k_plan(const __grid_constant__ BatchParams P, int threads, int grid,
+                       int* first_dev) {
+    if (threadIdx.x != 0) return;
+    int64_t want[kMaxBatch];
+    for (int i = 0; i < P.n_items; ++i)
+        want[i] = group_want(P.n_dev[P.item[i].slot], P.item[i].K, threads);
+    split_groups(want, P.n_items, grid, first_dev);
+}
+
 // One visited entry: distance, and the update with the later entry winning ties.
 #define WSM_VISIT(e, jj)                                        \
     {                                                           \
@@ -152,16 +204,20 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
         }                                                       \
     }
 
-template <bool kMap>
-__global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(const __grid_constant__ BatchParams P) {
+template <bool kMap, int kThreads>
+__global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sortmeans(const __grid_constant__ BatchParams P) {
     // ---- this block's image and group
-    int ii = 0;
-    while (ii + 1 < P.n_items && (int)blockIdx.x >= P.first_blk[ii + 1]) ++ii;
+    const int* first_blk = P.first_dev ? P.first_dev : P.first_blk;
+    if ((int)blockIdx.x >= first_blk[P.n_items]) return;   // not needed by any image
+    const int ii = item_of_block(first_blk, P.n_items, blockIdx.x);
     const ItemDesc I = P.item[ii];
-    const int G = P.first_blk[ii + 1] - P.first_blk[ii];
-    const int b = blockIdx.x - P.first_blk[ii];
+    const int G = first_blk[ii + 1] - first_blk[ii];
+    const int b = blockIdx.x - first_blk[ii];
     const int K = I.K;
-    const int64_t n = I.n;
+    const int64_t n = P.n_dev ? P.n_dev[I.slot] : I.n;
+    // sizes from the device were checked by the initialisation, which flagged
+    // an image with fewer unique colors than K; such an image is skipped
+    if (P.n_dev && n < K) return;
     const size_t kk = (size_t)P.sc.max_K * P.sc.max_K, s5 = (size_t)5 * P.sc.max_K;
     float4* const tab = P.sc.tab + (size_t)I.slot * kk;
     uint8_t* const tab_nb = P.sc.tab_nb + (size_t)I.slot * kk;
@@ -181,7 +237,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(const __grid_cons
     unsigned* s_acc = reinterpret_cast<unsigned*>(s_cn + KM);                 // [5KM] sums, max
     float* s_thr = reinterpret_cast<float*>(s_acc + 5 * KM);                  // [KM] row bounds
     unsigned long long* s_wkey = reinterpret_cast<unsigned long long*>(s_thr + KM);  // [WPB][KM]
-    __shared__ unsigned long long s_red[4][kIterThreads / 32];
+    __shared__ unsigned long long s_red[4][kThreads / 32];
     __shared__ int s_stop;
 
     const int copy = b % kCopies;
@@ -458,71 +514,48 @@ __global__ void __launch_bounds__(kIterThreads, 2) k_sortmeans(const __grid_cons
 #undef WSM_VISIT
 
 // Dynamic shared memory of k_sortmeans for palettes of up to KM colors.
-static size_t sortmeans_smem(int KM) {
-    return (size_t)KM * (16 + 16 + 20 + 4) + (size_t)(kIterThreads / 32) * KM * 8;
+static size_t sortmeans_smem(int KM, int threads) {
+    return (size_t)KM * (16 + 16 + 20 + 4) + (size_t)(threads / 32) * KM * 8;
 }
 
-// Co-residency of the persistent kernel: blocks per SM for the largest K.
+// The launch shapes of the persistent kernel: threads per block and blocks
+// per SM (the grid is that many blocks on every SM, all co-resident).
+const IterShape kIterShapes[kNumIterShapes] = {{512, 2}, {256, 4}, {1024, 1}, {256, 2}, {512, 1}};
+
+static void* sortmeans_fn(bool map_mode, int threads) {
+    switch (threads) {
+        case 256: return map_mode ? (void*)k_sortmeans<true, 256> : (void*)k_sortmeans<false, 256>;
+        case 1024: return map_mode ? (void*)k_sortmeans<true, 1024> : (void*)k_sortmeans<false, 1024>;
+        default: return map_mode ? (void*)k_sortmeans<true, 512> : (void*)k_sortmeans<false, 512>;
+    }
+}
+
+// Residency of each launch shape for palettes of up to max_K colors; the
+// handle starts with the first shape that fits.
 int iterate_kernel_setup(wsm_handle* h) {
-    int occ_it = 0, occ_map = 0;
-    const size_t smem = sortmeans_smem(h->max_K);
-    cudaError_t e = cudaFuncSetAttribute(k_sortmeans<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sortmeans<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_it, k_sortmeans<false>,
-                                                          kIterThreads, smem);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_map, k_sortmeans<true>,
-                                                          kIterThreads, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-    int occ = std::min(occ_it, occ_map);
-    if (occ < 1) return fail(WSM_E_CUDA, "persistent kernel cannot be resident");
-    h->iter_blocks_per_sm = std::min(occ, 2);
-    h->iter_grid = h->iter_blocks_per_sm * h->sms;
+    h->iter_shape = -1;
+    for (int q = 0; q < kNumIterShapes; ++q) {
+        const IterShape& sh = kIterShapes[q];
+        const size_t smem = sortmeans_smem(h->max_K, sh.threads);
+        int occ = 1 << 30;
+        for (int m = 0; m < 2; ++m) {
+            void* fn = sortmeans_fn(m == 1, sh.threads);
+            int o = 0;
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, sh.threads, smem);
+            if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+            occ = std::min(occ, o);
+        }
+        h->shape_ok[q] = occ >= sh.blocks_per_sm;
+        if (h->shape_ok[q] && h->iter_shape < 0) h->iter_shape = q;
+    }
+    if (h->iter_shape < 0) return fail(WSM_E_CUDA, "persistent kernel cannot be resident");
     return WSM_OK;
 }
 
-// Blocks of one image's group: enough for every lane to hold a color and for
-// every warp to hold a table row, within the available blocks.
-static int64_t group_want(int64_t n, int K) {
-    const int64_t for_colors = (n + kIterThreads - 1) / kIterThreads;
-    const int64_t for_rows = (K + kIterThreads / 32 - 1) / (kIterThreads / 32);
-    return std::max<int64_t>(1, std::max(for_colors, for_rows));
-}
-
-// Split `grid` co-resident blocks into one group per image, proportional to
-// each image's need (at least one block each); returns the total used.
-static int split_groups(const ItemDesc* items, int n_items, int grid, int* first_blk) {
-    std::vector<int64_t> want(n_items);
-    int64_t total = 0;
-    for (int i = 0; i < n_items; ++i) {
-        want[i] = group_want(items[i].n, items[i].K);
-        total += want[i];
-    }
-    std::vector<int> g(n_items, 1);
-    if (total <= grid) {
-        for (int i = 0; i < n_items; ++i) g[i] = (int)want[i];
-    } else {
-        int left = grid - n_items;
-        std::vector<std::pair<double, int>> frac;
-        for (int i = 0; i < n_items; ++i) {
-            const double share = (double)left * (double)(want[i] - 1) / (double)(total - n_items);
-            const int add = (int)share;
-            g[i] += add;
-            frac.push_back({share - add, i});
-        }
-        int used = 0;
-        for (int i = 0; i < n_items; ++i) used += g[i];
-        std::sort(frac.begin(), frac.end(), [](auto& a, auto& c) { return a.first > c.first; });
-        for (size_t q = 0; q < frac.size() && used < grid; ++q, ++used) g[frac[q].second] += 1;
-    }
-    first_blk[0] = 0;
-    for (int i = 0; i < n_items; ++i) first_blk[i + 1] = first_blk[i] + g[i];
-    return first_blk[n_items];
-}
+int iter_grid(const wsm_handle* h) { return kIterShapes[h->iter_shape].blocks_per_sm * h->sms; }
 
 static Scratch handle_scratch(wsm_handle* h) {
     Scratch sc;
@@ -538,24 +571,29 @@ static Scratch handle_scratch(wsm_handle* h) {
     return sc;
 }
 
-// One cooperative launch over n_items <= kMaxBatch images (item i in slot
-// i, or in the slots given).  grid_cap limits the blocks used.
+// One cooperative launch over n_items <= kMaxBatch images (item i in the
+// slot it names) with `threads` per block on at most grid_cap blocks.  With
+// n_dev the image sizes are read on the device (n_dev[slot]), k_plan writes
+// the split to first_dev ([kMaxBatch + 1]) and the whole grid_cap is
+// launched; otherwise the host splits the blocks.
 int launch_batch(const Scratch& sc, unsigned* status, bool map_mode, const ItemDesc* items,
-                 int n_items, int max_iter, double eps, int grid_cap, cudaStream_t s) {
+                 int n_items, int max_iter, double eps, int threads, int grid_cap,
+                 const int64_t* n_dev, int* first_dev, cudaStream_t s) {
     BatchParams P;
     P.sc = sc;
     P.status = status;
     P.n_items = n_items;
     P.max_iter = max_iter;
     P.eps = eps;
-    int KM = 1;
+    P.n_dev = n_dev;
+    P.first_dev = n_dev ? first_dev : nullptr;
+    int64_t want[kMaxBatch];
     for (int i = 0; i < n_items; ++i) {
         P.item[i] = items[i];
-        KM = std::max(KM, items[i].K);
+        want[i] = group_want(items[i].n, items[i].K, threads);
     }
-    const int grid = split_groups(items, n_items, grid_cap, P.first_blk);
+    const int grid = n_dev ? grid_cap : split_groups(want, n_items, grid_cap, P.first_blk);
     void* args[] = {&P};
-    void* fn = map_mode ? (void*)k_sortmeans<true> : (void*)k_sortmeans<false>;
     // Clear the barrier counters and the accumulators of the slots used.  The
     // items of a launch use consecutive slots, so one memset per array does.
     int lo = items[0].slot, hi = items[0].slot;
@@ -571,10 +609,14 @@ int launch_batch(const Scratch& sc, unsigned* status, bool map_mode, const ItemD
     if (e == cudaSuccess)
         e = cudaMemsetAsync(sc.sums64 + (size_t)lo * 2 * kCopies * 4, 0,
                             sizeof(unsigned long long) * 2 * kCopies * 4 * nsl, s);
+    if (e == cudaSuccess && n_dev) {
+        k_plan<<<1, 32, 0, s>>>(P, threads, grid, first_dev);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess)
-        e = cudaLaunchCooperativeKernel(fn, grid, kIterThreads, args, sortmeans_smem(sc.max_K), s);
+        e = cudaLaunchCooperativeKernel(sortmeans_fn(map_mode, threads), grid, threads, args,
+                                        sortmeans_smem(sc.max_K, threads), s);
     if (e != cudaSuccess) return cuda_fail(e, "sort-means launch");
-    (void)KM;
     return WSM_OK;
 }
 
@@ -590,25 +632,51 @@ int launch_sortmeans(wsm_handle* h, bool map_mode, const uint32_t* colors, const
     it.K = K;
     it.slot = 0;
     return launch_batch(handle_scratch(h), &h->ctrl->status, map_mode, &it, 1, max_iter, eps,
-                        h->iter_grid, s);
+                        kIterShapes[h->iter_shape].threads, iter_grid(h), nullptr, nullptr, s);
 }
 
 // The final assignment of n_items images (slots slot0, slot0 + 1, ...) in
 // one persistent launch in map mode.
 int launch_map_items(wsm_handle* h, const wsm_item* items, int n_items, int slot0,
-                     cudaStream_t s) {
+                     const int64_t* n_dev, cudaStream_t s) {
     ItemDesc d[kMaxBatch];
     for (int q = 0; q < n_items; ++q) {
         d[q].colors = items[q].d_colors;
         d[q].counts = nullptr;
         d[q].labels = items[q].d_labels;
         d[q].centers = reinterpret_cast<float4*>(items[q].d_centers);
-        d[q].n = items[q].n_unique;
+        d[q].n = n_dev ? items[q].n_pixels : items[q].n_unique;
         d[q].K = items[q].K;
         d[q].slot = slot0 + q;
     }
     return launch_batch(handle_scratch(h), &h->ctrl->status, true, d, n_items, 1, 0.0,
-                        h->iter_grid, s);
+                        kIterShapes[h->iter_shape].threads, iter_grid(h), n_dev,
+                        h->plan + (size_t)(slot0 / kMaxBatch) * (kMaxBatch + 1), s);
+}
+
+// The iterations of n_items images (item i in slot i), one persistent launch
+// per kMaxBatch images; with n_dev the sizes are read on the device.
+int iterate_items(wsm_handle* h, const wsm_item* items, int n_items, int max_iter, double eps,
+                  const int64_t* n_dev, cudaStream_t s) {
+    for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
+        const int m = std::min(kMaxBatch, n_items - i0);
+        ItemDesc d[kMaxBatch];
+        for (int q = 0; q < m; ++q) {
+            const wsm_item& it = items[i0 + q];
+            d[q].colors = it.d_colors;
+            d[q].counts = it.d_counts;
+            d[q].labels = it.d_labels;
+            d[q].centers = reinterpret_cast<float4*>(it.d_centers);
+            d[q].n = n_dev ? it.n_pixels : it.n_unique;   // an upper bound in device mode
+            d[q].K = it.K;
+            d[q].slot = i0 + q;
+        }
+        int rc = launch_batch(handle_scratch(h), &h->ctrl->status, false, d, m, max_iter, eps,
+                              kIterShapes[h->iter_shape].threads, iter_grid(h), n_dev,
+                              h->plan + (size_t)(i0 / kMaxBatch) * (kMaxBatch + 1), s);
+        if (rc != WSM_OK) return rc;
+    }
+    return WSM_OK;
 }
 
 // Checks of one batch item shared by the iterate and map entry points.
@@ -684,23 +752,8 @@ extern "C" int wsm_iterate_batch(wsm_handle* h, const wsm_item* items, int n_ite
         if (rc != WSM_OK) return rc;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
-        const int m = std::min(kMaxBatch, n_items - i0);
-        ItemDesc d[kMaxBatch];
-        for (int q = 0; q < m; ++q) {
-            const wsm_item& it = items[i0 + q];
-            d[q].colors = it.d_colors;
-            d[q].counts = it.d_counts;
-            d[q].labels = it.d_labels;
-            d[q].centers = reinterpret_cast<float4*>(it.d_centers);
-            d[q].n = it.n_unique;
-            d[q].K = it.K;
-            d[q].slot = i0 + q;
-        }
-        rc = launch_batch(handle_scratch(h), &h->ctrl->status, false, d, m, max_iter, eps,
-                          h->iter_grid, s);
-        if (rc != WSM_OK) return rc;
-    }
+    rc = iterate_items(h, items, n_items, max_iter, eps, nullptr, s);
+    if (rc != WSM_OK) return rc;
     if (iters_done && n_items > 0) {
         rc = read_status(h, s);
         if (rc != WSM_OK) return rc;
@@ -748,6 +801,7 @@ extern "C" int wsm_iterate_stats(wsm_handle* h, int K, int64_t* evaluated, int64
 namespace wsm {
 
 constexpr int kStaticMaxK = WSM_MAX_K;
+constexpr int kStaticThreads = 512;
 constexpr int kStaticMaxGrid = 1024;           // co-resident blocks used at most
 constexpr size_t kStaticTabBytes = sizeof(float4) * kStaticMaxK * kStaticMaxK;   // 1 MiB
 constexpr size_t kStaticNbBytes = (size_t)kStaticMaxK * kStaticMaxK;            // 64 KiB
@@ -787,11 +841,13 @@ static int static_setup(int dev, StaticSetup** out) {
         int sms = 0, occ = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_sortmeans<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sortmeans_smem(kStaticMaxK));
+            e = cudaFuncSetAttribute(k_sortmeans<false, kStaticThreads>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sortmeans_smem(kStaticMaxK, kStaticThreads));
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &occ, k_sortmeans<false>, kIterThreads, sortmeans_smem(kStaticMaxK));
+                &occ, k_sortmeans<false, kStaticThreads>, kStaticThreads,
+                sortmeans_smem(kStaticMaxK, kStaticThreads));
         if (e != cudaSuccess) return cuda_fail(e, "static set-up query");
         if (occ < 1) return fail(WSM_E_CUDA, "persistent kernel cannot be resident");
         st.scratch = static_cast<unsigned char*>(p);
@@ -849,7 +905,8 @@ extern "C" int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_c
     it.n = n_unique;
     it.K = K;
     it.slot = 0;
-    rc = launch_batch(sc, &ctrl->status, false, &it, 1, max_iter, eps, st->grid, s);
+    rc = launch_batch(sc, &ctrl->status, false, &it, 1, max_iter, eps, kStaticThreads, st->grid,
+                      nullptr, nullptr, s);
     if (rc != WSM_OK) return rc;
     if (iters_done || sse_trace) {
         Ctrl host;

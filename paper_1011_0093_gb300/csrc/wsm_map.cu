@@ -12,11 +12,6 @@
 
 namespace wsm {
 
-int launch_sortmeans(wsm_handle* h, bool map_mode, const uint32_t* colors, const uint32_t* counts,
-                     int64_t n, int K, float* centers, uint8_t* labels, int max_iter, double eps,
-                     cudaStream_t s);
-int check_item(wsm_handle* h, const wsm_item& it, bool need_pixels, bool need_counts);
-int launch_map_items(wsm_handle* h, const wsm_item* items, int n_items, int slot0, cudaStream_t s);
 
 __global__ void __launch_bounds__(256) k_gather(const uint8_t* __restrict__ rgb, int64_t n,
                                                 int stride, const uint8_t* __restrict__ lut,
@@ -181,6 +176,76 @@ __global__ void k_mse_final_batch(const __grid_constant__ MseItems B) {
     }
 }
 
+// The final assignment and the gather of n_items images (item i in slot i):
+// per kMaxBatch images one persistent launch in map mode and one gather.
+int map_items(wsm_handle* h, const wsm_item* items, int n_items, const int64_t* n_dev,
+              cudaStream_t s) {
+    for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
+        const int m = std::min(kMaxBatch, n_items - i0);
+        int rc = launch_map_items(h, items + i0, m, i0, n_dev, s);
+        if (rc != WSM_OK) return rc;
+        GatherBatch B;
+        B.n_items = m;
+        B.lut = h->lut;
+        int64_t total = 0;
+        for (int q = 0; q < m; ++q) total += items[i0 + q].n_pixels;
+        const int64_t budget = (int64_t)h->sms * 16;
+        B.first_blk[0] = 0;
+        for (int q = 0; q < m; ++q) {
+            const wsm_item& it = items[i0 + q];
+            B.rgb[q] = it.d_rgb;
+            B.index[q] = it.d_index;
+            B.n[q] = it.n_pixels;
+            B.stride[q] = it.pixel_stride;
+            B.slot[q] = i0 + q;
+            const int64_t want = (it.n_pixels + 255) / 256;
+            const int64_t share = std::max<int64_t>(1, budget * it.n_pixels / std::max<int64_t>(total, 1));
+            B.first_blk[q + 1] = B.first_blk[q] + (int)std::min(want, share);
+        }
+        k_gather_batch<<<B.first_blk[m], 256, 0, s>>>(B);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "gather launch");
+    }
+    return WSM_OK;
+}
+
+// Eq. 2 for n_items images (item i's MSE to batch_mse[i] and, if d_mse is
+// given, d_mse[i]): per kMaxBatch images one pair of launches.
+int distortion_items(wsm_handle* h, const wsm_item* items, int n_items, double* d_mse,
+                     cudaStream_t s) {
+    for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
+        MseItems B;
+        B.n_items = std::min(kMaxBatch, n_items - i0);
+        B.part = reinterpret_cast<unsigned long long*>(h->mse_part);
+        B.status = &h->ctrl->status;
+        int64_t total = 0;
+        for (int q = 0; q < B.n_items; ++q) total += items[i0 + q].n_pixels;
+        // at most 4 blocks per SM in all (and no more than the partial-sum
+        // buffer holds), split in proportion to pixels, >= 1 block per image
+        const int64_t budget = std::min<int64_t>(kMseMaxBlocks - kMaxBatch, 4 * (int64_t)h->sms);
+        B.first_blk[0] = 0;
+        for (int q = 0; q < B.n_items; ++q) {
+            const wsm_item& it = items[i0 + q];
+            B.rgb[q] = it.d_rgb;
+            B.n[q] = it.n_pixels;
+            B.stride[q] = it.pixel_stride;
+            B.centers[q] = reinterpret_cast<const float4*>(it.d_centers);
+            B.K[q] = it.K;
+            B.index[q] = it.d_index;
+            B.out[q] = h->batch_mse + i0 + q;
+            B.user[q] = d_mse ? d_mse + i0 + q : nullptr;
+            const int64_t want = (it.n_pixels + 4 * kMseThreads - 1) / (4 * kMseThreads);
+            const int64_t share = std::max<int64_t>(1, budget * it.n_pixels / total);
+            B.first_blk[q + 1] = B.first_blk[q] + (int)std::min(want, share);
+        }
+        k_mse_partial_batch<<<B.first_blk[B.n_items], kMseThreads, 0, s>>>(B);
+        k_mse_final_batch<<<B.n_items, 32, 0, s>>>(B);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "distortion launch");
+    }
+    return WSM_OK;
+}
+
 }  // namespace wsm
 
 using namespace wsm;
@@ -224,34 +289,7 @@ extern "C" int wsm_map_batch(wsm_handle* h, const wsm_item* items, int n_items,
         rc = check_item(h, items[i], true, false);
         if (rc != WSM_OK) return rc;
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
-        const int m = std::min(kMaxBatch, n_items - i0);
-        rc = launch_map_items(h, items + i0, m, i0, s);
-        if (rc != WSM_OK) return rc;
-        GatherBatch B;
-        B.n_items = m;
-        B.lut = h->lut;
-        int64_t total = 0;
-        for (int q = 0; q < m; ++q) total += items[i0 + q].n_pixels;
-        const int64_t budget = (int64_t)h->sms * 16;
-        B.first_blk[0] = 0;
-        for (int q = 0; q < m; ++q) {
-            const wsm_item& it = items[i0 + q];
-            B.rgb[q] = it.d_rgb;
-            B.index[q] = it.d_index;
-            B.n[q] = it.n_pixels;
-            B.stride[q] = it.pixel_stride;
-            B.slot[q] = i0 + q;
-            const int64_t want = (it.n_pixels + 255) / 256;
-            const int64_t share = std::max<int64_t>(1, budget * it.n_pixels / std::max<int64_t>(total, 1));
-            B.first_blk[q + 1] = B.first_blk[q] + (int)std::min(want, share);
-        }
-        k_gather_batch<<<B.first_blk[m], 256, 0, s>>>(B);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "gather launch");
-    }
-    return WSM_OK;
+    return map_items(h, items, n_items, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels,
@@ -311,36 +349,8 @@ extern "C" int wsm_distortion_batch(wsm_handle* h, const wsm_item* items, int n_
     }
     if (n_items == 0) return WSM_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
-        MseItems B;
-        B.n_items = std::min(kMaxBatch, n_items - i0);
-        B.part = reinterpret_cast<unsigned long long*>(h->mse_part);
-        B.status = &h->ctrl->status;
-        int64_t total = 0;
-        for (int q = 0; q < B.n_items; ++q) total += items[i0 + q].n_pixels;
-        // at most 4 blocks per SM in all (and no more than the partial-sum
-        // buffer holds), split in proportion to pixels, >= 1 block per image
-        const int64_t budget = std::min<int64_t>(kMseMaxBlocks - kMaxBatch, 4 * (int64_t)h->sms);
-        B.first_blk[0] = 0;
-        for (int q = 0; q < B.n_items; ++q) {
-            const wsm_item& it = items[i0 + q];
-            B.rgb[q] = it.d_rgb;
-            B.n[q] = it.n_pixels;
-            B.stride[q] = it.pixel_stride;
-            B.centers[q] = reinterpret_cast<const float4*>(it.d_centers);
-            B.K[q] = it.K;
-            B.index[q] = it.d_index;
-            B.out[q] = h->batch_mse + i0 + q;
-            B.user[q] = d_mse ? d_mse + i0 + q : nullptr;
-            const int64_t want = (it.n_pixels + 4 * kMseThreads - 1) / (4 * kMseThreads);
-            const int64_t share = std::max<int64_t>(1, budget * it.n_pixels / total);
-            B.first_blk[q + 1] = B.first_blk[q] + (int)std::min(want, share);
-        }
-        k_mse_partial_batch<<<B.first_blk[B.n_items], kMseThreads, 0, s>>>(B);
-        k_mse_final_batch<<<B.n_items, 32, 0, s>>>(B);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "distortion launch");
-    }
+    rc = distortion_items(h, items, n_items, d_mse, s);
+    if (rc != WSM_OK) return rc;
     if (mse) {
         cudaError_t e = cudaMemcpyAsync(h->host_mse, h->batch_mse, sizeof(double) * n_items,
                                         cudaMemcpyDeviceToHost, s);

@@ -1,0 +1,160 @@
+// wsm_pipeline.cu -- the whole path for a batch of images with no host
+// synchronisation, and the autotuner of the persistent kernel's launch shape.
+//
+// wsm_quantize_batch runs unique colors (Sec. 2) -> initialisation
+// (Algorithm 2, first step) -> the Sort-Means iterations with the Sec. 3.2
+// stop rule -> final assignment and pixel mapping (Sec. 1) -> MSE (Eq. 2)
+// for every image, stream-ordered.  The number of unique colors N' of each
+// image stays on the device: the initialisation draws its Floyd sample from
+// it there, and the persistent launches split their blocks from it there
+// (k_plan), so the host never waits and the whole sequence can be captured
+// into a CUDA graph and replayed on new pixels.
+//
+// wsm_autotune_batch times every resident launch shape (threads per block x
+// blocks per SM) of the persistent kernel on a batch and keeps the fastest
+// for the handle; every shape gives the same results bit for bit (the
+// reductions are exact), so the choice is about time only.
+#include <algorithm>
+#include <vector>
+
+#include "wsm_internal.cuh"
+
+namespace wsm {
+
+__global__ void k_outputs(int n_items, const int64_t* __restrict__ nu, const Ctrl* __restrict__ ctrl,
+                          int64_t* __restrict__ d_n_unique, int* __restrict__ d_iters) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_items; i += gridDim.x * blockDim.x) {
+        if (d_n_unique) d_n_unique[i] = nu[i];
+        if (d_iters) d_iters[i] = ctrl[i].iters_done;
+    }
+}
+
+static int check_batch(wsm_handle* h, const wsm_item* items, int n_items, const uint64_t* seeds,
+                       int max_iter) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (n_items < 0 || (n_items > 0 && (!items || !seeds))) return fail(WSM_E_INVAL, "bad item list");
+    if (n_items > h->slots)
+        return fail(WSM_E_INVAL, "more items than reserved slots (wsm_reserve_batch)");
+    if (max_iter < 0 || max_iter > kMaxTrace)
+        return fail(WSM_E_INVAL, "max_iter must be in [0, 4096]");
+    for (int i = 0; i < n_items; ++i) {
+        const wsm_item& it = items[i];
+        rc = check_pixels(h, it);
+        if (rc != WSM_OK) return rc;
+        if (it.K < 1 || it.K > h->max_K) return fail(WSM_E_INVAL, "K out of [1, max_K]");
+        if (!it.d_colors || !it.d_counts || !it.d_centers || !it.d_labels || !it.d_index)
+            return fail(WSM_E_INVAL, "null device pointer");
+        if ((uintptr_t)it.d_centers & 15) return fail(WSM_E_INVAL, "centers must be 16-byte aligned");
+    }
+    return WSM_OK;
+}
+
+}  // namespace wsm
+
+using namespace wsm;
+
+extern "C" int wsm_quantize_batch(wsm_handle* h, const wsm_item* items, int n_items,
+                                  const uint64_t* seeds, int max_iter, double eps,
+                                  int64_t* d_n_unique, int* d_iters, double* d_mse,
+                                  wsm_stream stream) {
+    int rc = check_batch(h, items, n_items, seeds, max_iter);
+    if (rc != WSM_OK) return rc;
+    if (n_items == 0) return WSM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = reduce_items(h, items, n_items, s);
+    if (rc == WSM_OK) rc = init_items_dev(h, items, n_items, seeds, s);
+    if (rc == WSM_OK) rc = iterate_items(h, items, n_items, max_iter, eps, h->batch_nu, s);
+    if (rc != WSM_OK) return rc;
+    if (d_n_unique || d_iters) {   // before the mapping launch resets the slots' counters
+        k_outputs<<<(n_items + 255) / 256, 256, 0, s>>>(n_items, h->batch_nu, h->slot_ctrl,
+                                                         d_n_unique, d_iters);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "output launch");
+    }
+    rc = map_items(h, items, n_items, h->batch_nu, s);
+    if (rc == WSM_OK) rc = distortion_items(h, items, n_items, d_mse, s);
+    return rc;
+}
+
+extern "C" int wsm_set_launch_shape(wsm_handle* h, int shape) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (shape < 0 || shape >= kNumIterShapes) return fail(WSM_E_INVAL, "shape out of range");
+    if (!h->shape_ok[shape])
+        return fail(WSM_E_INVAL, "that launch shape cannot be resident at this handle's max_K");
+    h->iter_shape = shape;
+    return WSM_OK;
+}
+
+extern "C" int wsm_launch_shape(wsm_handle* h, int shape, int* threads, int* blocks_per_sm,
+                                int* resident) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (shape < 0) shape = h->iter_shape;
+    if (shape >= kNumIterShapes) return fail(WSM_E_INVAL, "shape out of range");
+    if (threads) *threads = kIterShapes[shape].threads;
+    if (blocks_per_sm) *blocks_per_sm = kIterShapes[shape].blocks_per_sm;
+    if (resident) *resident = h->shape_ok[shape] ? 1 : 0;
+    return shape;
+}
+
+extern "C" int wsm_autotune_batch(wsm_handle* h, const wsm_item* items, int n_items,
+                                  const uint64_t* seeds, int max_iter, double eps, int repeats,
+                                  float* times_ms, wsm_stream stream) {
+    int rc = check_batch(h, items, n_items, seeds, max_iter);
+    if (rc != WSM_OK) return rc;
+    if (n_items == 0) return h->iter_shape;
+    if (repeats < 1 || repeats > 100) return fail(WSM_E_INVAL, "repeats must be in [1, 100]");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return cuda_fail(e, "autotune events");
+    }
+    const int saved = h->iter_shape;
+    int best = -1;
+    float best_ms = 0.f;
+    rc = reduce_items(h, items, n_items, s);
+    for (int q = 0; q < kNumIterShapes && rc == WSM_OK; ++q) {
+        float t_min = -1.f;
+        if (h->shape_ok[q]) {
+            h->iter_shape = q;
+            for (int r = 0; r < repeats && rc == WSM_OK; ++r) {
+                // the initialisation restores the starting centers and labels
+                rc = init_items_dev(h, items, n_items, seeds, s);
+                if (rc != WSM_OK) break;
+                e = cudaEventRecord(a, s);
+                if (e == cudaSuccess) {
+                    rc = iterate_items(h, items, n_items, max_iter, eps, h->batch_nu, s);
+                    if (rc != WSM_OK) break;
+                    e = cudaEventRecord(b, s);
+                }
+                if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "autotune timing");
+                    break;
+                }
+                if (t_min < 0.f || ms < t_min) t_min = ms;
+            }
+            if (rc == WSM_OK && (best < 0 || t_min < best_ms)) {
+                best = q;
+                best_ms = t_min;
+            }
+        }
+        if (times_ms) times_ms[q] = t_min;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc == WSM_OK) rc = read_status(h, s);
+    if (rc != WSM_OK || best < 0) {
+        h->iter_shape = saved;
+        return rc != WSM_OK ? rc : fail(WSM_E_CUDA, "no launch shape could be timed");
+    }
+    h->iter_shape = best;
+    return best;
+}

@@ -189,6 +189,42 @@ static int launch_reduce(wsm_handle* h, ReduceItems& R, cudaStream_t s) {
     return WSM_OK;
 }
 
+// Unique colors of n_items images (item i's N' to batch_nu[i]), one launch of
+// each reduction kernel per h->rslots images; colors and counts of item i
+// have room for its n_pixels entries.
+int reduce_items(wsm_handle* h, const wsm_item* items, int n_items, cudaStream_t s) {
+    for (int i0 = 0; i0 < n_items; i0 += h->rslots) {
+        ReduceItems R;
+        R.n_items = std::min(h->rslots, n_items - i0);
+        for (int q = 0; q < R.n_items; ++q) {
+            const wsm_item& it = items[i0 + q];
+            R.rgb[q] = it.d_rgb;
+            R.n[q] = it.n_pixels;
+            R.stride[q] = it.pixel_stride;
+            R.colors[q] = const_cast<uint32_t*>(it.d_colors);
+            R.counts[q] = const_cast<uint32_t*>(it.d_counts);
+            R.capacity[q] = it.n_pixels;
+            R.n_out[q] = h->batch_nu + i0 + q;
+            R.n_user[q] = nullptr;
+        }
+        int rc = launch_reduce(h, R, s);
+        if (rc != WSM_OK) return rc;
+    }
+    return WSM_OK;
+}
+
+// Checks of the pixel fields of a batch item (reduction, mapping, distortion).
+int check_pixels(wsm_handle* h, const wsm_item& it) {
+    if (it.pixel_stride != 3 && it.pixel_stride != 4)
+        return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
+    if (it.n_pixels < 1 || it.n_pixels > h->max_pixels)
+        return fail(WSM_E_INVAL, "n_pixels must be in [1, max_pixels]");
+    if (!it.d_rgb) return fail(WSM_E_INVAL, "null pixel pointer");
+    if (it.pixel_stride == 4 && ((uintptr_t)it.d_rgb & 3))
+        return fail(WSM_E_INVAL, "4-byte pixels must be 4-byte aligned");
+    return WSM_OK;
+}
+
 }  // namespace wsm
 
 using namespace wsm;
@@ -238,33 +274,13 @@ extern "C" int wsm_reduce_batch(wsm_handle* h, wsm_item* items, int n_items, wsm
     if (n_items > h->slots)
         return fail(WSM_E_INVAL, "more items than reserved slots (wsm_reserve_batch)");
     for (int i = 0; i < n_items; ++i) {
-        const wsm_item& it = items[i];
-        if (it.pixel_stride != 3 && it.pixel_stride != 4)
-            return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
-        if (it.n_pixels < 1 || it.n_pixels > h->max_pixels)
-            return fail(WSM_E_INVAL, "n_pixels must be in [1, max_pixels]");
-        if (!it.d_rgb || !it.d_colors || !it.d_counts) return fail(WSM_E_INVAL, "null device pointer");
-        if (it.pixel_stride == 4 && ((uintptr_t)it.d_rgb & 3))
-            return fail(WSM_E_INVAL, "4-byte pixels must be 4-byte aligned");
+        rc = check_pixels(h, items[i]);
+        if (rc != WSM_OK) return rc;
+        if (!items[i].d_colors || !items[i].d_counts) return fail(WSM_E_INVAL, "null device pointer");
     }
     cudaStream_t s = (cudaStream_t)stream;
-    for (int i0 = 0; i0 < n_items; i0 += h->rslots) {
-        ReduceItems R;
-        R.n_items = std::min(h->rslots, n_items - i0);
-        for (int q = 0; q < R.n_items; ++q) {
-            const wsm_item& it = items[i0 + q];
-            R.rgb[q] = it.d_rgb;
-            R.n[q] = it.n_pixels;
-            R.stride[q] = it.pixel_stride;
-            R.colors[q] = const_cast<uint32_t*>(it.d_colors);
-            R.counts[q] = const_cast<uint32_t*>(it.d_counts);
-            R.capacity[q] = it.n_pixels;
-            R.n_out[q] = h->batch_nu + i0 + q;
-            R.n_user[q] = nullptr;
-        }
-        rc = launch_reduce(h, R, s);
-        if (rc != WSM_OK) return rc;
-    }
+    rc = reduce_items(h, items, n_items, s);
+    if (rc != WSM_OK) return rc;
     if (n_items == 0) return WSM_OK;
     cudaError_t e = cudaMemcpyAsync(h->host_nu, h->batch_nu, sizeof(int64_t) * n_items,
                                     cudaMemcpyDeviceToHost, s);
