@@ -16,6 +16,10 @@ Workload (one step): 8 seeded 512x512 RGB images (noise amplitude swept
   cpu_baseline  the CPU oracle on a bounded sample of the same workload.
 
 ``--impl reference`` times the CPU oracle instead (the reference arm).
+``--form batch`` times the batched form instead: 64 seeded images with sides
+log-uniform in [256, 2048], K = 256, WSM 10 iterations, the whole path as one
+replay of a captured CUDA graph (launch shape from the autotuner), against
+64 sequential runs of the one-image path on the same images.
 ``--form grad`` times the differentiable form instead: forward + backward of
 the weighted distortion D(C, X) of a 512x512 image's pixels at K = 64, and
 200 Adam steps of palette refinement from the WSM palette.
@@ -532,13 +536,148 @@ def run_grad(args):
     h.close()
 
 
+BATCH_COUNT = 64
+BATCH_SEED = 3
+
+
+def _batch_image(args):
+    q, (h, w) = args
+    return synth.image(h, w, 7000 + q, (5 * q) % 25)
+
+
+def batch_workload():
+    """64 images, sides log-uniform in [256, 2048] (seeded), noise 0..24, built
+    by a pool of spawned processes (no CUDA state is shared)."""
+    import multiprocessing as mp
+    sizes = synth.batch_sizes(BATCH_SEED, BATCH_COUNT, 256, 2048)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_batch_image, list(enumerate(sizes)))
+
+
+def run_batch(args):
+    """Batched form: one graph replay per step vs the one-image path."""
+    images = batch_workload()                     # before any CUDA call
+    import torch
+
+    import paper_1011_0093_gb300 as wsm
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    n_img = len(images)
+    seeds = [9000 + q for q in range(n_img)]
+    h_imgs = [torch.from_numpy(im).pin_memory() for im in images]
+    d_imgs = [t.to(dev) for t in h_imgs]
+    plan = wsm.BatchPlan([im.shape for im in images], K_PALETTE, seeds, max_iter=ITERS)
+    plan.load(d_imgs)
+    best, shape_ms = plan.tune(repeats=2)
+    evaluated, _ = plan.stats()
+    shapes = [wsm.wsm_launch_shape(plan.handle, q)[1:3] for q in range(len(shape_ms))]
+    plan.capture()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        plan.replay()
+    plan.sync()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.replay()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    plan.sync()
+    # end to end: pixels up from pinned host memory, index images, palettes and
+    # MSE back, around the same replay
+    out_idx = [torch.empty(im.shape[:2], dtype=torch.uint8).pin_memory() for im in images]
+    out_pal = torch.empty((n_img, K_PALETTE, 4), dtype=torch.float32).pin_memory()
+    out_mse = torch.empty(n_img, dtype=torch.float64).pin_memory()
+    e2e = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.load(h_imgs)
+        plan.replay()
+        for q in range(n_img):
+            out_idx[q].copy_(plan.images[q]["index"], non_blocking=True)
+            out_pal[q].copy_(plan.images[q]["centers"], non_blocking=True)
+        out_mse.copy_(plan.mse, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    plan.sync()
+    # the one-image path, image after image, on the same device-resident inputs
+    h1 = wsm.Handle(K_PALETTE, max(im.shape[0] * im.shape[1] for im in images))
+    seq = []
+    same = True
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        outs = [wsm.quantize(d_imgs[q], K_PALETTE, seeds[q], max_iter=ITERS, handle=h1)
+                for q in range(n_img)]
+        torch.cuda.synchronize()
+        seq.append((time.perf_counter() - t0) * 1e3)
+    for q, o in enumerate(outs):
+        r = plan.result(q)
+        same &= (torch.equal(o.centers, r["centers"]) and torch.equal(o.index, r["index"])
+                 and o.mse == r["mse"] and o.iters == r["iters"])
+    n_unique = [plan.result(q)["n_unique"] for q in range(n_img)]
+    step_ms = statistics.median(ms)
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    it_ms = shape_ms[best]
+    tflops = 8.0 * sum(evaluated) / (it_ms * 1e-3) / 1e12
+    chunks16, chunks48 = -(-n_img // 16), -(-n_img // 48)
+    launches = 3 * chunks16 + 1 * chunks48 + 2 * chunks48 + 1 + 3 * chunks48 + 2 * chunks48
+    line = {
+        "metric": "batched WSM: images/s, 64 images 256^2..2048^2, K=256, one CUDA-graph replay",
+        "form": "batch", "value": n_img / (step_ms * 1e-3), "unit": "images/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{n_img} images, sides log-uniform in [256, 2048] (seed "
+                               f"{BATCH_SEED}), noise 0..24, K=256, WSM 10 iterations",
+                   "pixels": int(sum(im.shape[0] * im.shape[1] for im in images)),
+                   "unique_colors_min_max": [min(n_unique), max(n_unique)],
+                   "unique_colors_total": int(sum(n_unique)),
+                   "l2": "flushed between steps (256 MiB write)"},
+        "e2e": {"value": n_img / (statistics.median(e2e) * 1e-3), "unit": "images/s",
+                "h2d_bytes_per_step": int(sum(im.nbytes for im in images)),
+                "d2h_bytes_per_step": int(sum(im.shape[0] * im.shape[1] for im in images)
+                                          + n_img * (K_PALETTE * 16 + 8))},
+        "sequential_one_image_path": {"ms": min(seq), "images_per_s": n_img / (min(seq) * 1e-3),
+                                      "speedup": min(seq) / step_ms,
+                                      "identical_results": bool(same)},
+        "autotune": {"chosen": {"threads": shapes[best][0], "blocks_per_sm": shapes[best][1]},
+                     "iterate_ms_by_shape": {f"{t}x{b}": m for (t, b), m in zip(shapes, shape_ms)}},
+        "roofline": {"bound": "alu", "kernel": "k_sortmeans<iterate> (all launches of the batch)",
+                     "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": tflops / fp32_peak, "traffic": None,
+                     "peak_kind": "FP32 SMs x 128 x 2 x max SM clock",
+                     "flop": 8.0 * sum(evaluated), "launch_ms": it_ms},
+        "cpu_baseline": None, "clocks": clk,
+        "gpu_launches": launches * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    h1.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wsm", choices=["wsm", "reference"])
-    ap.add_argument("--form", default="plain", choices=["plain", "grad"])
+    ap.add_argument("--form", default="plain", choices=["plain", "grad", "batch"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -548,6 +687,8 @@ def main():
         run_reference(args)
     elif args.form == "grad":
         run_grad(args)
+    elif args.form == "batch":
+        run_batch(args)
     else:
         run_gpu(args)
 

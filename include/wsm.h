@@ -313,6 +313,16 @@ WSM_API int wsm_quantize_batch(wsm_handle* h, const wsm_item* items, int n_items
                                int64_t* d_n_unique, int* d_iters, double* d_mse,
                                wsm_stream stream);
 
+/* Counters of the last persistent launch over image slots 0..n_items-1
+ * (an iterate launch, or the final assignment of a mapping, which resets
+ * them): distances evaluated (1 + visited row entries per color and pass)
+ * and iterations run.  Synchronises the stream.
+ *   evaluated  host int64 [n_items] (may be NULL); iters host int [n_items]
+ *              (may be NULL)
+ * Errors: WSM_E_INVAL (n_items > reserved slots), or a pending device error. */
+WSM_API int wsm_batch_stats(wsm_handle* h, int n_items, int64_t* evaluated, int* iters,
+                            wsm_stream stream);
+
 /* Launch shapes of the persistent Sort-Means kernel (no counterpart in the
  * paper: a GPU launch parameter).  Shape s = (threads per block, blocks per
  * SM); the persistent launches of the handle use its current shape.  Every

@@ -15,7 +15,8 @@ from ._native import (MAX_K, MAX_PIXELS, Handle, WsmError, lib, wsm_distortion,
                       wsm_iterate_batch, wsm_iterate_noalloc, wsm_iterate_stats, wsm_map,
                       wsm_map_batch, wsm_reduce, wsm_reduce_batch, wsm_reserve_batch,
                       wsm_sync_status, wsm_quantize_batch, wsm_autotune_batch,
-                      wsm_launch_shape, wsm_set_launch_shape, pipeline_items)
+                      wsm_launch_shape, wsm_set_launch_shape, wsm_batch_stats,
+                      pipeline_items)
 from .batch import BatchPlan
 from .distortion import WeightedDistortion, weighted_distortion
 from .quantize import Quantized, quantize, quantize_batch
@@ -25,6 +26,6 @@ __all__ = ["MAX_K", "MAX_PIXELS", "Handle", "WsmError", "lib", "wsm_reduce", "ws
            "wsm_map_batch", "wsm_reserve_batch", "wsm_reduce_batch", "wsm_init_batch",
            "wsm_distortion_batch", "wsm_distortion_fwd", "wsm_distortion_bwd",
            "WeightedDistortion", "weighted_distortion", "wsm_quantize_batch",
-           "wsm_autotune_batch", "wsm_launch_shape", "wsm_set_launch_shape", "pipeline_items",
+           "wsm_autotune_batch", "wsm_launch_shape", "wsm_set_launch_shape", "wsm_batch_stats", "pipeline_items",
            "BatchPlan", "wsm_map", "wsm_distortion", "wsm_sync_status",
            "Quantized", "quantize", "quantize_batch"]

@@ -59,6 +59,7 @@ SIGNATURES = {
     "wsm_launch_shape": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                    C.POINTER(C.c_int)]),
     "wsm_set_launch_shape": (C.c_int, [_P, C.c_int]),
+    "wsm_batch_stats": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "wsm_autotune_batch": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_double, C.c_int, _P, _P]),
     "wsm_distortion_fwd": (C.c_int, [_P, _P, C.c_int, _P, _I64, _P, C.c_int, C.c_int, _P,
                                      C.c_int, _P, _P, _P]),
@@ -474,3 +475,12 @@ def wsm_autotune_batch(h: Handle, items, n_items: int, seeds, max_iter: int, eps
                                               int(repeats), C.cast(times, C.c_void_p),
                                               _stream(stream)))
     return q, [times[i] for i in range(N_SHAPES)]
+
+
+def wsm_batch_stats(h: Handle, n_items: int, stream=None) -> tuple[list[int], list[int]]:
+    """(distances evaluated, iterations) of the last persistent launch per slot."""
+    ev = (C.c_int64 * max(n_items, 1))()
+    it = (C.c_int * max(n_items, 1))()
+    _check(lib().wsm_batch_stats(h.ptr, int(n_items), C.cast(ev, C.c_void_p),
+                                 C.cast(it, C.c_void_p), _stream(stream)))
+    return [ev[i] for i in range(n_items)], [it[i] for i in range(n_items)]

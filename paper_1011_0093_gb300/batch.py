@@ -62,6 +62,11 @@ class BatchPlan:
         return N.wsm_autotune_batch(self.handle, self._items, self.n_items, self._seeds,
                                     self.max_iter, self.eps, repeats)
 
+    def stats(self):
+        """(distances evaluated, iterations) per image of the last persistent
+        launch (after tune(): of the Sort-Means iterations)."""
+        return N.wsm_batch_stats(self.handle, self.n_items)
+
     def capture(self):
         """Capture run() into a CUDA graph (after one eager run to warm up)."""
         side = torch.cuda.Stream(device=self.device)

@@ -77,6 +77,25 @@ extern "C" int wsm_quantize_batch(wsm_handle* h, const wsm_item* items, int n_it
     return rc;
 }
 
+extern "C" int wsm_batch_stats(wsm_handle* h, int n_items, int64_t* evaluated, int* iters,
+                               wsm_stream stream) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (n_items < 0 || n_items > h->slots) return fail(WSM_E_INVAL, "n_items out of [0, slots]");
+    if (n_items == 0) return WSM_OK;
+    rc = read_status(h, (cudaStream_t)stream);
+    if (rc != WSM_OK) return rc;
+    std::vector<Ctrl> c(n_items);
+    cudaError_t e = cudaMemcpy(c.data(), h->slot_ctrl, sizeof(Ctrl) * n_items,
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "stats copy");
+    for (int i = 0; i < n_items; ++i) {
+        if (evaluated) evaluated[i] = (int64_t)c[i].evaluated;
+        if (iters) iters[i] = c[i].iters_done;
+    }
+    return WSM_OK;
+}
+
 extern "C" int wsm_set_launch_shape(wsm_handle* h, int shape) {
     int rc = check_handle(h);
     if (rc != WSM_OK) return rc;
