@@ -20,6 +20,9 @@ Workload (one step): 8 seeded 512x512 RGB images (noise amplitude swept
 log-uniform in [256, 2048], K = 256, WSM 10 iterations, the whole path as one
 replay of a captured CUDA graph (launch shape from the autotuner), against
 64 sequential runs of the one-image path on the same images.
+``--form serve`` drives the native serving loop instead: Poisson arrivals of
+requests drawn from 48 seeded images with sides log-uniform in [128, 4096]
+and K in {16, 64, 256}; p50/p99 latency and images/s over 10k requests.
 ``--form grad`` times the differentiable form instead: forward + backward of
 the weighted distortion D(C, X) of a 512x512 image's pixels at K = 64, and
 200 Adam steps of palette refinement from the WSM palette.
@@ -671,13 +674,121 @@ def run_batch(args):
     h1.close()
 
 
+SERVE_BANK = 48
+
+
+def _serve_image(args):
+    q, (h, w) = args
+    return synth.image(h, w, 11000 + q, (7 * q) % 25)
+
+
+def serve_workload():
+    """48 images, sides log-uniform in [128, 4096] (seeded), noise 0..24."""
+    import multiprocessing as mp
+    sizes = synth.batch_sizes(5, SERVE_BANK, 128, 4096)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_serve_image, list(enumerate(sizes)))
+
+
+def _drive(srv, bank, plan, rate):
+    """Submit the planned requests (bank index, K, seed) at Poisson times of
+    the given rate (None: all at once) and collect them; per-request latency
+    from the server's own clock, and the throughput over the whole run."""
+    import threading
+    rng = np.random.default_rng(23)
+    gaps = rng.exponential(1.0 / rate, len(plan)) if rate else np.zeros(len(plan))
+    pending = []
+    lock = threading.Condition()
+
+    def submitter():
+        t = time.perf_counter()
+        for (b, K, seed), g in zip(plan, gaps):
+            t += g
+            d = t - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            p = srv.submit(bank[b], K, seed)
+            with lock:
+                pending.append(p)
+                lock.notify()
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, first, last = [], None, None
+    for i in range(len(plan)):
+        with lock:
+            while len(pending) <= i:
+                lock.wait()
+            p = pending[i]
+            pending[i] = None
+        r = srv.wait(p)
+        lat.append(r["latency"])
+        first = r["t_submit"] if first is None else min(first, r["t_submit"])
+        last = r["t_done"] if last is None else max(last, r["t_done"])
+    th.join()
+    lat = np.array(lat) * 1e3
+    return {"requests": len(plan), "offered_rate": rate, "images_per_s": len(plan) / (last - first),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean())}
+
+
+def run_serve(args):
+    bank_np = serve_workload()                    # before any CUDA call
+    import torch
+
+    import paper_1011_0093_gb300 as wsm
+
+    torch.cuda.set_device(0)
+    bank = [torch.from_numpy(im).pin_memory() for im in bank_np]
+    rng = np.random.default_rng(19)
+    n_req = args.requests
+
+    def plan(n):
+        return [(int(rng.integers(0, len(bank))), int(rng.choice([16, 64, 256])),
+                 int(rng.integers(0, 1 << 40))) for _ in range(n)]
+
+    with wsm.Server(lanes=args.lanes, slots_per_lane=16, arena_bytes=8 << 30) as srv:
+        _drive(srv, bank, plan(2 * SERVE_BANK), None)              # warm-up
+        sat = _drive(srv, bank, plan(min(n_req, 2000)), None)      # closed loop: capacity
+        clocks = ClockSampler(0)
+        clocks.start()
+        main = _drive(srv, bank, plan(n_req), 0.8 * sat["images_per_s"])
+        clk = clocks.stop()
+        sweep = [_drive(srv, bank, plan(min(n_req, 1500)), f * sat["images_per_s"])
+                 for f in (0.3, 0.6, 0.95)]
+        st = srv.stats()
+    px = [im.shape[0] * im.shape[1] for im in bank_np]
+    line = {
+        "metric": "serving: images/s and p50/p99 latency, Poisson arrivals, images 128^2..4096^2",
+        "form": "serve", "value": main["images_per_s"], "unit": "images/s", "n_gpus": 1,
+        "steps": n_req, "warmup": 2 * SERVE_BANK, "ms_per_step": main["mean_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{n_req} requests drawn from {len(bank)} seeded images (sides "
+                               "log-uniform in [128, 4096], noise 0..24), K in {16, 64, 256}, "
+                               "WSM 10 iterations; Poisson arrivals at 0.8x the closed-loop "
+                               "capacity", "pixels_min_max": [min(px), max(px)],
+                   "lanes": args.lanes, "slots_per_lane": 16, "arena_bytes": 8 << 30},
+        "latency_ms": {"p50": main["p50_ms"], "p99": main["p99_ms"], "mean": main["mean_ms"]},
+        "capacity_closed_loop": sat, "rate_sweep": sweep,
+        "server": st,
+        "e2e": {"value": main["images_per_s"], "unit": "images/s",
+                "h2d_bytes_per_step": int(np.mean([im.nbytes for im in bank_np])),
+                "d2h_bytes_per_step": int(np.mean(px))},
+        "cpu_baseline": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wsm", choices=["wsm", "reference"])
-    ap.add_argument("--form", default="plain", choices=["plain", "grad", "batch"])
+    ap.add_argument("--form", default="plain", choices=["plain", "grad", "batch", "serve"])
+    ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--lanes", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -689,6 +800,8 @@ def main():
         run_grad(args)
     elif args.form == "batch":
         run_batch(args)
+    elif args.form == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

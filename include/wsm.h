@@ -336,6 +336,12 @@ WSM_API int wsm_launch_shape(wsm_handle* h, int shape, int* threads, int* blocks
                              int* resident);
 WSM_API int wsm_set_launch_shape(wsm_handle* h, int shape);
 
+/* Limits every persistent launch of the handle to `blocks` blocks (0: the
+ * whole co-resident grid of its shape), so that several handles on several
+ * streams can run their persistent launches side by side on one GPU.
+ * Errors: WSM_E_INVAL (0 < blocks < 48). */
+WSM_API int wsm_set_grid_limit(wsm_handle* h, int blocks);
+
 /* Autotuner: runs the unique-color reduction of the batch once, then for
  * every resident shape `repeats` times the initialisation (untimed) and the
  * Sort-Means iterations (timed with CUDA events on `stream`), and makes the
@@ -347,6 +353,78 @@ WSM_API int wsm_set_launch_shape(wsm_handle* h, int shape);
 WSM_API int wsm_autotune_batch(wsm_handle* h, const wsm_item* items, int n_items,
                                const uint64_t* seeds, int max_iter, double eps, int repeats,
                                float* times_ms, wsm_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of quantization requests (no counterpart in
+ * the paper, which quantizes one image at a time).  A server owns `lanes`
+ * lanes -- each a stream, a handle limited to 1/lanes of the SMs and up to
+ * slots_per_lane images per batch -- and a device arena of arena_bytes for
+ * the requests' buffers.  A scheduler thread admits queued requests first
+ * come, first served, into idle lanes while slots and arena memory allow
+ * (a request needs about 14 bytes per pixel, see wsm_server_submit), runs
+ * each lane's batch as wsm_quantize_batch with the copies in and out on the
+ * lane's stream, and completes the requests when the lane's event fires.
+ * Lanes overlap on the device; a request's results are the same alone and
+ * in any mix (the per-image computation does not depend on the batch).
+ * ------------------------------------------------------------------------- */
+typedef struct wsm_server wsm_server;
+
+typedef struct {
+    int max_K;               /* 1..256 */
+    int64_t max_pixels;      /* per request, 1..2^24 */
+    int lanes;               /* 1..8 */
+    int slots_per_lane;      /* 1..48 */
+    int64_t arena_bytes;     /* device memory for the requests' buffers */
+} wsm_server_config;
+
+typedef struct {
+    const uint8_t* rgb;      /* host [n_pixels][pixel_stride]; page-locked for overlap */
+    int64_t n_pixels;
+    int pixel_stride;        /* 3 or 4 */
+    int K;
+    uint64_t seed;           /* initialisation seed (as wsm_init) */
+    int max_iter;            /* requests with other (max_iter, eps) go to other batches */
+    double eps;
+    uint8_t* index_out;      /* host [n_pixels] (may be NULL); page-locked for overlap */
+    float* palette_out;      /* host [K][4] (may be NULL); page-locked for overlap */
+} wsm_request;
+
+typedef struct {
+    int status;              /* WSM_OK, or the request's error (N' < K: WSM_E_INVAL) */
+    int iters;
+    int64_t n_unique;
+    double mse;
+    double t_submit, t_admit, t_done;   /* steady-clock seconds */
+} wsm_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, batches;
+    int64_t in_flight, max_in_flight, queued;
+    int64_t arena_bytes, arena_used, arena_peak;
+} wsm_server_stats;
+
+/* Creates the lanes, the arena and the scheduler thread on the current
+ * device.  Errors: WSM_E_INVAL (config), WSM_E_NOMEM, WSM_E_CUDA. */
+WSM_API int wsm_server_create(wsm_server** out, const wsm_server_config* cfg);
+
+/* Queues a request (thread-safe, does not block).  The host buffers must
+ * stay valid until wsm_server_wait returns for it.  Footprint in the arena:
+ * the pixels, 4 + 4 bytes per pixel for colors and counts, 1 + 1 for labels
+ * and index, 16 K for the palette, each rounded up to 256 bytes.
+ * Errors: WSM_E_INVAL (sizes), WSM_E_CAPACITY (footprint > arena),
+ * WSM_E_STATE (shutting down). */
+WSM_API int wsm_server_submit(wsm_server* s, const wsm_request* r, uint64_t* id);
+
+/* Waits for request `id` (timeout_s < 0: no limit) and returns its result;
+ * the id is then forgotten.  The index image and palette are in the
+ * request's output buffers.  Returns the request's status, WSM_E_TIMEOUT if
+ * it is not done in time (it stays queued), WSM_E_INVAL for an unknown id. */
+WSM_API int wsm_server_wait(wsm_server* s, uint64_t id, double timeout_s, wsm_result* res);
+
+WSM_API int wsm_server_stats_get(wsm_server* s, wsm_server_stats* st);
+
+/* Completes every queued request, then frees the server. */
+WSM_API int wsm_server_destroy(wsm_server* s);
 
 /* The weighted distortion of Eq. 1 (the k-means objective) with the sample
  * weights of Sec. 2, as a differentiable function of the palette C and of

@@ -6,6 +6,7 @@ sm_103a behind the C ABI of include/wsm.h (libwsm.so).  This package is the
 thin Python layer above it: ``_native`` marshals arguments to the C entry
 points; ``quantize`` chains them for one image or a batch; ``batch`` holds a
 fixed batch's buffers and captures the whole path into a CUDA graph;
+``serve`` queues requests to the native continuous-batching server;
 ``distortion`` wraps the weighted distortion and its gradients as a
 torch.autograd.Function.  PyTorch only provides device memory and streams.
 """
@@ -16,8 +17,9 @@ from ._native import (MAX_K, MAX_PIXELS, Handle, WsmError, lib, wsm_distortion,
                       wsm_map_batch, wsm_reduce, wsm_reduce_batch, wsm_reserve_batch,
                       wsm_sync_status, wsm_quantize_batch, wsm_autotune_batch,
                       wsm_launch_shape, wsm_set_launch_shape, wsm_batch_stats,
-                      pipeline_items)
+                      wsm_set_grid_limit, pipeline_items)
 from .batch import BatchPlan
+from .serve import Server
 from .distortion import WeightedDistortion, weighted_distortion
 from .quantize import Quantized, quantize, quantize_batch
 
@@ -26,6 +28,6 @@ __all__ = ["MAX_K", "MAX_PIXELS", "Handle", "WsmError", "lib", "wsm_reduce", "ws
            "wsm_map_batch", "wsm_reserve_batch", "wsm_reduce_batch", "wsm_init_batch",
            "wsm_distortion_batch", "wsm_distortion_fwd", "wsm_distortion_bwd",
            "WeightedDistortion", "weighted_distortion", "wsm_quantize_batch",
-           "wsm_autotune_batch", "wsm_launch_shape", "wsm_set_launch_shape", "wsm_batch_stats", "pipeline_items",
-           "BatchPlan", "wsm_map", "wsm_distortion", "wsm_sync_status",
+           "wsm_autotune_batch", "wsm_launch_shape", "wsm_set_launch_shape", "wsm_batch_stats", "wsm_set_grid_limit", "pipeline_items",
+           "BatchPlan", "Server", "wsm_map", "wsm_distortion", "wsm_sync_status",
            "Quantized", "quantize", "quantize_batch"]

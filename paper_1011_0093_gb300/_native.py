@@ -36,6 +36,33 @@ class WsmItem(C.Structure):
                 ("d_index", C.c_void_p)]
 
 
+class ServerConfig(C.Structure):
+    """wsm_server_config of include/wsm.h."""
+    _fields_ = [("max_K", C.c_int), ("max_pixels", C.c_int64), ("lanes", C.c_int),
+                ("slots_per_lane", C.c_int), ("arena_bytes", C.c_int64)]
+
+
+class Request(C.Structure):
+    """wsm_request of include/wsm.h."""
+    _fields_ = [("rgb", C.c_void_p), ("n_pixels", C.c_int64), ("pixel_stride", C.c_int),
+                ("K", C.c_int), ("seed", C.c_uint64), ("max_iter", C.c_int),
+                ("eps", C.c_double), ("index_out", C.c_void_p), ("palette_out", C.c_void_p)]
+
+
+class Result(C.Structure):
+    """wsm_result of include/wsm.h."""
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("n_unique", C.c_int64),
+                ("mse", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    """wsm_server_stats of include/wsm.h."""
+    _fields_ = [(name, C.c_int64) for name in
+                ("submitted", "completed", "failed", "batches", "in_flight", "max_in_flight",
+                 "queued", "arena_bytes", "arena_used", "arena_peak")]
+
+
 SIGNATURES = {
     "wsm_last_error": (C.c_char_p, []),
     "wsm_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _I64, _I64]),
@@ -60,6 +87,12 @@ SIGNATURES = {
                                    C.POINTER(C.c_int)]),
     "wsm_set_launch_shape": (C.c_int, [_P, C.c_int]),
     "wsm_batch_stats": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "wsm_set_grid_limit": (C.c_int, [_P, C.c_int]),
+    "wsm_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(ServerConfig)]),
+    "wsm_server_submit": (C.c_int, [_P, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "wsm_server_wait": (C.c_int, [_P, C.c_uint64, C.c_double, C.POINTER(Result)]),
+    "wsm_server_stats_get": (C.c_int, [_P, C.POINTER(ServerStats)]),
+    "wsm_server_destroy": (C.c_int, [_P]),
     "wsm_autotune_batch": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_double, C.c_int, _P, _P]),
     "wsm_distortion_fwd": (C.c_int, [_P, _P, C.c_int, _P, _I64, _P, C.c_int, C.c_int, _P,
                                      C.c_int, _P, _P, _P]),
@@ -484,3 +517,7 @@ def wsm_batch_stats(h: Handle, n_items: int, stream=None) -> tuple[list[int], li
     _check(lib().wsm_batch_stats(h.ptr, int(n_items), C.cast(ev, C.c_void_p),
                                  C.cast(it, C.c_void_p), _stream(stream)))
     return [ev[i] for i in range(n_items)], [it[i] for i in range(n_items)]
+
+
+def wsm_set_grid_limit(h: Handle, blocks: int):
+    _check(lib().wsm_set_grid_limit(h.ptr, int(blocks)))

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwsm.so")
 SOURCES = ["wsm_api.cu", "wsm_reduce.cu", "wsm_iterate.cu", "wsm_map.cu", "wsm_grad.cu",
-           "wsm_pipeline.cu"]
+           "wsm_pipeline.cu", "wsm_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          "-I", INCLUDE, "-I", CSRC]

@@ -149,8 +149,12 @@ __global__ void __launch_bounds__(256) k_init_dev(const __grid_constant__ InitDe
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t n = B.n_dev[i];
     const int K = B.K[i];
-    if (n < K) {
-        if (j == 0 && tid == 0) atomicOr(B.status, ST_FEW_COLORS);
+    if (n < K) {                                    // skipped: zero centers, flagged
+        if (j == 0) {
+            for (int k = tid; k < K; k += blockDim.x)
+                B.centers[i][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (tid == 0) atomicOr(B.status, ST_FEW_COLORS);
+        }
         return;
     }
     for (int64_t q = (int64_t)j * blockDim.x + tid; q < n; q += (int64_t)kInitBlocks * blockDim.x)

@@ -67,6 +67,7 @@ struct wsm_handle {
     int64_t max_pixels = 0;
     int64_t max_unique = 0;
     int iter_shape = 0;          // index into kIterShapes used by the persistent launches
+    int grid_limit = 0;          // > 0: at most this many blocks per persistent launch
     bool shape_ok[wsm::kNumIterShapes] = {};   // shapes whose blocks can all be resident
     // scratch (device)
     double* mse_part = nullptr;  // [1024] block partials + [1] result
@@ -130,7 +131,7 @@ int launch_map_items(wsm_handle* h, const wsm_item* items, int n_items, int slot
 int map_items(wsm_handle* h, const wsm_item* items, int n_items, const int64_t* n_dev,
               cudaStream_t s);
 int distortion_items(wsm_handle* h, const wsm_item* items, int n_items, double* d_mse,
-                     cudaStream_t s);
+                     const int64_t* n_dev, cudaStream_t s);
 void free_slots(wsm_handle* h);
 
 // ---------------------------------------------------------------------------

@@ -555,7 +555,12 @@ int iterate_kernel_setup(wsm_handle* h) {
     return WSM_OK;
 }
 
-int iter_grid(const wsm_handle* h) { return kIterShapes[h->iter_shape].blocks_per_sm * h->sms; }
+// Blocks of the persistent launches: the shape's full co-resident grid, or
+// fewer if the handle is limited to a share of the GPU.
+int iter_grid(const wsm_handle* h) {
+    const int full = kIterShapes[h->iter_shape].blocks_per_sm * h->sms;
+    return h->grid_limit > 0 ? std::min(full, h->grid_limit) : full;
+}
 
 static Scratch handle_scratch(wsm_handle* h) {
     Scratch sc;

@@ -31,7 +31,9 @@ struct GatherBatch {
     int64_t n[kMaxBatch];
     int stride[kMaxBatch];
     int slot[kMaxBatch];
+    int K[kMaxBatch];
     const uint8_t* lut;        // slot s at lut + s * 2^24
+    const int64_t* n_dev;      // if set: an image with n_dev[slot] < K was skipped (index 0)
 };
 
 __global__ void __launch_bounds__(256) k_gather_batch(const __grid_constant__ GatherBatch B) {
@@ -39,9 +41,10 @@ __global__ void __launch_bounds__(256) k_gather_batch(const __grid_constant__ Ga
     const int g0 = B.first_blk[i], G = B.first_blk[i + 1] - g0;
     const uint8_t* lut = B.lut + (size_t)B.slot[i] * kHistBins;
     const int64_t n = B.n[i];
+    const bool skipped = B.n_dev && B.n_dev[B.slot[i]] < B.K[i];
     for (int64_t p = (int64_t)(blockIdx.x - g0) * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)G * blockDim.x)
-        B.index[i][p] = lut[pixel_key(B.rgb[i], p, B.stride[i])];
+        B.index[i][p] = skipped ? 0 : lut[pixel_key(B.rgb[i], p, B.stride[i])];
 }
 
 constexpr int kMseThreads = 256;
@@ -124,6 +127,7 @@ struct MseItems {
     double* user[kMaxBatch];    // MSE (device), a caller's copy, may be null
     unsigned long long* part;   // one partial sum per block of the launch
     unsigned* status;
+    const int64_t* n_dev;       // if set: an image with n_dev[i] < K[i] was skipped (MSE 0)
 };
 
 // Per-block fixed-point sums as in k_mse_partial, for the image owning the block.
@@ -137,11 +141,13 @@ __global__ void __launch_bounds__(kMseThreads) k_mse_partial_batch(const __grid_
     const uint8_t* index = B.index[i];
     const int64_t n = B.n[i];
     const int stride = B.stride[i];
+    const bool skipped = B.n_dev && B.n_dev[i] < K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) s_c[k] = B.centers[i][k];
     __syncthreads();
     unsigned long long acc = 0;
     bool bad = false;
-    for (int64_t p = (int64_t)g * blockDim.x + threadIdx.x; p < n; p += (int64_t)G * blockDim.x) {
+    for (int64_t p = (int64_t)g * blockDim.x + threadIdx.x; !skipped && p < n;
+         p += (int64_t)G * blockDim.x) {
         const int k = index[p];
         if (k >= K) {
             bad = true;
@@ -187,6 +193,7 @@ int map_items(wsm_handle* h, const wsm_item* items, int n_items, const int64_t* 
         GatherBatch B;
         B.n_items = m;
         B.lut = h->lut;
+        B.n_dev = n_dev;
         int64_t total = 0;
         for (int q = 0; q < m; ++q) total += items[i0 + q].n_pixels;
         const int64_t budget = (int64_t)h->sms * 16;
@@ -198,6 +205,7 @@ int map_items(wsm_handle* h, const wsm_item* items, int n_items, const int64_t* 
             B.n[q] = it.n_pixels;
             B.stride[q] = it.pixel_stride;
             B.slot[q] = i0 + q;
+            B.K[q] = it.K;
             const int64_t want = (it.n_pixels + 255) / 256;
             const int64_t share = std::max<int64_t>(1, budget * it.n_pixels / std::max<int64_t>(total, 1));
             B.first_blk[q + 1] = B.first_blk[q] + (int)std::min(want, share);
@@ -210,12 +218,14 @@ int map_items(wsm_handle* h, const wsm_item* items, int n_items, const int64_t* 
 }
 
 // Eq. 2 for n_items images (item i's MSE to batch_mse[i] and, if d_mse is
-// given, d_mse[i]): per kMaxBatch images one pair of launches.
+// given, d_mse[i]): per kMaxBatch images one pair of launches.  With n_dev,
+// an image skipped for N' < K gets MSE 0.
 int distortion_items(wsm_handle* h, const wsm_item* items, int n_items, double* d_mse,
-                     cudaStream_t s) {
+                     const int64_t* n_dev, cudaStream_t s) {
     for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
         MseItems B;
         B.n_items = std::min(kMaxBatch, n_items - i0);
+        B.n_dev = n_dev ? n_dev + i0 : nullptr;
         B.part = reinterpret_cast<unsigned long long*>(h->mse_part);
         B.status = &h->ctrl->status;
         int64_t total = 0;
@@ -349,7 +359,7 @@ extern "C" int wsm_distortion_batch(wsm_handle* h, const wsm_item* items, int n_
     }
     if (n_items == 0) return WSM_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    rc = distortion_items(h, items, n_items, d_mse, s);
+    rc = distortion_items(h, items, n_items, d_mse, nullptr, s);
     if (rc != WSM_OK) return rc;
     if (mse) {
         cudaError_t e = cudaMemcpyAsync(h->host_mse, h->batch_mse, sizeof(double) * n_items,

@@ -73,7 +73,7 @@ extern "C" int wsm_quantize_batch(wsm_handle* h, const wsm_item* items, int n_it
         if (e != cudaSuccess) return cuda_fail(e, "output launch");
     }
     rc = map_items(h, items, n_items, h->batch_nu, s);
-    if (rc == WSM_OK) rc = distortion_items(h, items, n_items, d_mse, s);
+    if (rc == WSM_OK) rc = distortion_items(h, items, n_items, d_mse, h->batch_nu, s);
     return rc;
 }
 
@@ -93,6 +93,15 @@ extern "C" int wsm_batch_stats(wsm_handle* h, int n_items, int64_t* evaluated, i
         if (evaluated) evaluated[i] = (int64_t)c[i].evaluated;
         if (iters) iters[i] = c[i].iters_done;
     }
+    return WSM_OK;
+}
+
+extern "C" int wsm_set_grid_limit(wsm_handle* h, int blocks) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (blocks != 0 && blocks < kMaxBatch)
+        return fail(WSM_E_INVAL, "a grid limit must be 0 (none) or at least 48 blocks");
+    h->grid_limit = blocks;
     return WSM_OK;
 }
 
