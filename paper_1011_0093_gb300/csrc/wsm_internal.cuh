@@ -43,20 +43,19 @@ struct IterShape {
 constexpr int kNumIterShapes = 5;
 extern const IterShape kIterShapes[kNumIterShapes];
 
-// Control words in device memory (one block per handle).
-// The fields before `status` are cleared before every persistent launch, so
-// a barrier abandoned after a timeout cannot confuse the next launch.
+// Control words in device memory: one for the handle (status word, N', MSE
+// mirror) and one per image slot (barrier counter, iteration and distance
+// counts, chunk tickets), the latter cleared before every persistent launch
+// so that a barrier abandoned after a timeout cannot confuse the next one.
 struct Ctrl {
     unsigned bar_count;        // grid barrier: monotonic arrival counter
     int iters_done;            // iterations completed by the last wsm_iterate
     unsigned long long evaluated;  // distances computed by the last persistent launch
     unsigned status;           // ST_* bits (cleared only when read by the host)
-    unsigned reserved;
+    unsigned ticket[2];        // chunks handed out in the assignment pass, by pass parity
     int64_t n_unique;          // N' of the last wsm_reduce
     double mse;                // host mirror slot of the last wsm_distortion
 };
-constexpr size_t kLaunchResetBytes = 16;
-static_assert(offsetof(Ctrl, status) == kLaunchResetBytes, "Ctrl layout");
 
 }  // namespace wsm
 

@@ -298,7 +298,19 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sortmeans(const _
         __syncthreads();
         unsigned long long sse_fx = 0, ev = 0, npix = 0, nonzero = 0;
         bool bad = false;
-        int64_t cur = first;
+        // Chunks: warp w of block b starts with chunk b * WPB + w, then takes
+        // chunks G * WPB + t in the order of the tickets t it draws from the
+        // slot's counter (each ticket drawn one chunk ahead), so the warps of
+        // the group finish together whatever the cost of their colors.
+        unsigned* const ticket = &ctrl->ticket[buf];
+        int64_t cur = ((int64_t)b * WPB + wid) * kChunk;
+        int64_t nxt = n;
+        {
+            unsigned t = 0;
+            if (lane == 0 && cur < n) t = atomicAdd(ticket, 1u);
+            t = __shfl_sync(0xFFFFFFFFu, t, 0);
+            if (cur < n) nxt = ((int64_t)G * WPB + t) * kChunk;
+        }
         uint32_t col_n = 0, cnt_n = 0;
         int lab_n = 0;
         if (cur + lane < n) {
@@ -306,17 +318,20 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sortmeans(const _
             lab_n = I.labels[cur + lane];
             if (!kMap) cnt_n = __ldg(I.counts + cur + lane);
         }
-        for (; cur < n; cur += stride) {
-            const int64_t nxt = cur + stride;
+        while (cur < n) {
             const int64_t i = cur + lane;
             const bool active = i < n;
             const uint32_t col = col_n;
             const unsigned cnt = cnt_n;
             const int p0 = lab_n;
-            if (nxt + lane < n) {
-                col_n = __ldg(I.colors + nxt + lane);
-                lab_n = I.labels[nxt + lane];
-                if (!kMap) cnt_n = __ldg(I.counts + nxt + lane);
+            unsigned t_after = 0;
+            if (nxt < n) {
+                if (nxt + lane < n) {
+                    col_n = __ldg(I.colors + nxt + lane);
+                    lab_n = I.labels[nxt + lane];
+                    if (!kMap) cnt_n = __ldg(I.counts + nxt + lane);
+                }
+                if (lane == 0) t_after = atomicAdd(ticket, 1u);   // used after this chunk
             }
             int p = p0;
             if (p >= K) {                          // invalid input membership
@@ -381,6 +396,9 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sortmeans(const _
                     nonzero += mn > 0.f;
                 }
             }
+            const unsigned t = __shfl_sync(0xFFFFFFFFu, t_after, 0);
+            cur = nxt;
+            nxt = cur < n ? ((int64_t)G * WPB + t) * kChunk : n;
         }
         if (bad) atomicOr(P.status, ST_BAD_LABEL);
         sse_fx = warp_sum_u64(sse_fx);
@@ -474,6 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sortmeans(const _
                 nxt[(size_t)c * s5 + r] = 0u;
             }
             if (tid < 4 * kCopies) sums64[(size_t)(buf ^ 1) * kCopies * 4 + tid] = 0ull;
+            if (tid == 0) ctrl->ticket[buf ^ 1] = 0u;   // drawn from two barriers ago
         }
         __syncthreads();
         {
