@@ -55,9 +55,10 @@ METRIC = "unique-color assignments/s per iter (K=256) vs FP32 peak; 512² images
 UNIT = "assignments/s"
 L2_FLUSH_BYTES = 256 << 20
 # per step, all images together: hist24, scan_count, scan_emit (up to 16 images
-# per launch), init, the sort-means launch, the map-mode sort-means launch, the
-# gather, mse_partial and mse_final (up to 48 images per launch)
-KERNELS_PER_STEP = 9
+# per launch), init, the plan kernel, the sort-means launch and the output copy
+# for the iterations, the plan kernel, the map-mode sort-means launch and the
+# gather for the mapping, mse_partial and mse_final (up to 48 images per launch)
+KERNELS_PER_STEP = 12
 
 
 def workload(rank: int):
@@ -229,8 +230,6 @@ def run_gpu(args):
     import torch.distributed as dist
 
     import paper_1011_0093_gb300 as wsm
-    from paper_1011_0093_gb300 import _native as nat
-
     world, rank, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -240,51 +239,37 @@ def run_gpu(args):
 
     images = workload(rank)
     n = H * W
-    d_imgs = [torch.from_numpy(im).to(dev) for im in images]
     h_imgs = [torch.from_numpy(im).pin_memory() for im in images]
-    handle = wsm.Handle(K_PALETTE, n, n)
-    wsm.wsm_reserve_batch(handle, len(images))
-    colors = [torch.empty(n, dtype=torch.uint32, device=dev) for _ in images]
-    counts = [torch.empty(n, dtype=torch.uint32, device=dev) for _ in images]
-    centers = [torch.empty((K_PALETTE, 4), dtype=torch.float32, device=dev) for _ in images]
-    labels = [torch.empty(n, dtype=torch.uint8, device=dev) for _ in images]
-    index = [torch.empty((H, W), dtype=torch.uint8, device=dev) for _ in images]
-    mse = torch.empty(len(images), dtype=torch.float64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    it_events = []          # (tag, start, end) around every batched iterate launch
     seeds = [image_seed(rank, s) for s in range(len(images))]
-    items = [dict(rgb=d_imgs[s], colors=colors[s], counts=counts[s], K=K_PALETTE,
-                  centers=centers[s], labels=labels[s], index=index[s])
-             for s in range(len(images))]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    plan = wsm.BatchPlan([im.shape for im in images], K_PALETTE, seeds, max_iter=ITERS)
+    plan.load(h_imgs)
+    # the iterations, once on their own: distances evaluated per image (the
+    # same every step: same inputs) for the roofline
+    plan.run(wsm.STAGE_REDUCE | wsm.STAGE_INIT | wsm.STAGE_ITERATE)
+    evaluated, _ = plan.stats()
+    # one step = three captured graphs replayed back to back: a1-a2, a3-a6
+    # (one persistent launch over the 8 images), a7-a8; events between them
+    # time the iterations inside the timed region
+    parts = (wsm.STAGE_REDUCE | wsm.STAGE_INIT, wsm.STAGE_ITERATE,
+             wsm.STAGE_MAP | wsm.STAGE_DISTORTION)
+    plan.capture(parts)
+    it_events = []
 
     def step(record: bool):
-        # every step of the path is one batched call over all images:
-        # a1 (one host sync for all N'), a2, a3-a6 (one persistent launch),
-        # a7 (one persistent launch + one gather), a8
-        wsm.wsm_reduce_batch(handle, items)
-        wsm.wsm_init_batch(handle, items, seeds)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)] if record else None
+        plan.replay(0)
         if record:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        wsm.wsm_iterate_batch(handle, items, ITERS, 0.0, sync=False)
+            e[0].record(stream)
+        plan.replay(1)
         if record:
-            e1.record(stream)
-            it_events.append((-1, e0, e1))
-        wsm.wsm_map_batch(handle, items)
-        wsm.wsm_distortion_batch(handle, items, d_mse=mse, sync=False)
+            e[1].record(stream)
+            it_events.append(e)
+        plan.replay(2)
 
-    # distances evaluated per image (deterministic: same inputs every step)
-    evaluated = []
-    for s in range(len(images)):
-        nu = wsm.wsm_reduce(handle, d_imgs[s], colors[s], counts[s])
-        wsm.wsm_init(handle, colors[s], nu, K_PALETTE, image_seed(rank, s), centers[s], labels[s])
-        done, _ = wsm.wsm_iterate(handle, colors[s], counts[s], nu, K_PALETTE, centers[s],
-                                  labels[s], ITERS, 0.0)
-        evaluated.append(wsm.wsm_iterate_stats(handle, K_PALETTE, sums=False)[0])
     for _ in range(args.warmup):
         step(False)
-    wsm.wsm_sync_status(handle)
+    plan.sync()
 
     def barrier():
         if world > 1:
@@ -305,11 +290,13 @@ def run_gpu(args):
         b.synchronize()
         step_ms.append(a.elapsed_time(b))
     barrier()
-    wsm.wsm_sync_status(handle)
-    units_step = sum(im["n_unique"] for im in items) * ITERS
+    plan.sync()
+    n_unique = [int(v) for v in plan.n_unique.cpu()]
+    units_step = sum(n_unique) * ITERS
     total_ms = sum(step_ms)
 
-    # e2e through the public API from pinned host memory
+    # e2e through the public API from pinned host memory: pixels up, then the
+    # same replay, then index images, palettes and MSE down
     e2e_ms = []
     h2d = sum(im.numel() for im in h_imgs)
     d2h = len(images) * (n + K_PALETTE * 16 + 8)
@@ -318,17 +305,12 @@ def run_gpu(args):
     out_mse = torch.empty(len(images), dtype=torch.float64).pin_memory()
 
     def e2e_step():
-        imgs = [himg.to(dev, non_blocking=True) for himg in h_imgs]
-        qs = wsm.quantize_batch(imgs, K_PALETTE, seeds, max_iter=ITERS, eps=0.0, handle=handle,
-                                mse=False)
-        wsm.wsm_distortion_batch(handle, [dict(rgb=img, K=K_PALETTE, centers=q.centers,
-                                               index=q.index) for img, q in zip(imgs, qs)],
-                                 d_mse=mse, sync=False)
-        for s, q in enumerate(qs):
-            out_idx[s].copy_(q.index, non_blocking=True)
-            out_pal[s].copy_(q.centers, non_blocking=True)
-        out_mse.copy_(mse, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        plan.load(h_imgs)
+        plan.replay()
+        for s in range(len(images)):
+            out_idx[s].copy_(plan.images[s]["index"], non_blocking=True)
+            out_pal[s].copy_(plan.images[s]["centers"], non_blocking=True)
+        out_mse.copy_(plan.mse, non_blocking=True)
 
     for _ in range(max(args.warmup, 1)):
         e2e_step()
@@ -345,11 +327,11 @@ def run_gpu(args):
         e2e_ms.append(a.elapsed_time(b))
     barrier()
     clk = clocks.stop()
+    plan.sync()
 
     # roofline of the persistent sort-means kernel, from the timed steps
-    it_ms = [e0.elapsed_time(e1) for _, e0, e1 in it_events]
-    it_flop = [8.0 * sum(evaluated) for _ in it_events]   # one launch covers all images
-    achieved_tflops = sum(it_flop) / (sum(it_ms) * 1e-3) / 1e12
+    it_ms = [e0.elapsed_time(e1) for e0, e1 in it_events]
+    achieved_tflops = 8.0 * sum(evaluated) * len(it_ms) / (sum(it_ms) * 1e-3) / 1e12
     pk, pk_kind = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -371,7 +353,7 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "sweep 8x512x512 noise 0..24 per GPU, K=256, WSM 10 iterations",
-                       "unique_colors": [im["n_unique"] for im in items],
+                       "unique_colors": n_unique,
                        "images_per_step": len(images) * world,
                        "images_per_s": len(images) * world * args.steps / (total_ms * 1e-3),
                        "images_per_s_e2e": len(images) * world * args.steps / (e2e_total * 1e-3),
@@ -385,13 +367,14 @@ def run_gpu(args):
                          "peak_kind": f"FP32 {sms} SMs x 128 x 2 x {pk.get('sm_max_mhz')} MHz "
                                       f"({pk_kind} max clock)",
                          "launch_ms": sum(it_ms) / len(it_ms),
-                         "flop_per_launch": sum(it_flop) / len(it_flop)},
+                         "flop_per_launch": 8.0 * sum(evaluated),
+                         "timed": "the iterate graph (plan kernel, counter clears, persistent "
+                                  "launch, output copy) between CUDA events in every step"},
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": KERNELS_PER_STEP * args.steps,
         }
         print(json.dumps(line), flush=True)
-    handle.close()
     if world > 1:
         dist.destroy_process_group()
 

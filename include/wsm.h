@@ -313,6 +313,27 @@ WSM_API int wsm_quantize_batch(wsm_handle* h, const wsm_item* items, int n_items
                                int64_t* d_n_unique, int* d_iters, double* d_mse,
                                wsm_stream stream);
 
+/* The stages of wsm_quantize_batch, for wsm_quantize_batch_stages. */
+enum {
+    WSM_STAGE_REDUCE = 1,      /* Sec. 2 unique colors (writes N' on the device) */
+    WSM_STAGE_INIT = 2,        /* Algorithm 2 initialisation (needs REDUCE before) */
+    WSM_STAGE_ITERATE = 4,     /* Sort-Means iterations, Sec. 3.2 stop rule; d_n_unique, d_iters */
+    WSM_STAGE_MAP = 8,         /* final assignment + pixel mapping */
+    WSM_STAGE_DISTORTION = 16, /* Eq. 2 MSE; d_mse */
+    WSM_STAGE_ALL = 31
+};
+
+/* The stages of wsm_quantize_batch named by the `stages` bits, in the order
+ * above, on the device state the earlier stages left (the handle's N'
+ * values, the items' buffers).  Running the stages in several calls, e.g. to
+ * time them or to capture each into its own CUDA graph, gives exactly the
+ * results of one wsm_quantize_batch call.
+ * Errors: as wsm_quantize_batch; WSM_E_INVAL for unknown stage bits. */
+WSM_API int wsm_quantize_batch_stages(wsm_handle* h, const wsm_item* items, int n_items,
+                                      const uint64_t* seeds, int max_iter, double eps,
+                                      int64_t* d_n_unique, int* d_iters, double* d_mse,
+                                      unsigned stages, wsm_stream stream);
+
 /* Counters of the last persistent launch over image slots 0..n_items-1
  * (an iterate launch, or the final assignment of a mapping, which resets
  * them): distances evaluated (1 + visited row entries per color and pass)

@@ -17,7 +17,8 @@ from ._native import (MAX_K, MAX_PIXELS, Handle, WsmError, lib, wsm_distortion,
                       wsm_map_batch, wsm_reduce, wsm_reduce_batch, wsm_reserve_batch,
                       wsm_sync_status, wsm_quantize_batch, wsm_autotune_batch,
                       wsm_launch_shape, wsm_set_launch_shape, wsm_batch_stats,
-                      wsm_set_grid_limit, pipeline_items)
+                      wsm_set_grid_limit, pipeline_items, STAGE_REDUCE, STAGE_INIT,
+                      STAGE_ITERATE, STAGE_MAP, STAGE_DISTORTION, STAGE_ALL)
 from .batch import BatchPlan
 from .serve import Server
 from .distortion import WeightedDistortion, weighted_distortion
@@ -28,6 +29,7 @@ __all__ = ["MAX_K", "MAX_PIXELS", "Handle", "WsmError", "lib", "wsm_reduce", "ws
            "wsm_map_batch", "wsm_reserve_batch", "wsm_reduce_batch", "wsm_init_batch",
            "wsm_distortion_batch", "wsm_distortion_fwd", "wsm_distortion_bwd",
            "WeightedDistortion", "weighted_distortion", "wsm_quantize_batch",
-           "wsm_autotune_batch", "wsm_launch_shape", "wsm_set_launch_shape", "wsm_batch_stats", "wsm_set_grid_limit", "pipeline_items",
+           "wsm_autotune_batch", "wsm_launch_shape", "wsm_set_launch_shape", "wsm_batch_stats", "wsm_set_grid_limit", "pipeline_items", "STAGE_REDUCE", "STAGE_INIT",
+           "STAGE_ITERATE", "STAGE_MAP", "STAGE_DISTORTION", "STAGE_ALL",
            "BatchPlan", "Server", "wsm_map", "wsm_distortion", "wsm_sync_status",
            "Quantized", "quantize", "quantize_batch"]

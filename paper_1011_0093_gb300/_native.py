@@ -83,6 +83,8 @@ SIGNATURES = {
     "wsm_init_batch": (C.c_int, [_P, _P, C.c_int, _P, _P]),
     "wsm_distortion_batch": (C.c_int, [_P, _P, C.c_int, _P, _P, _P]),
     "wsm_quantize_batch": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_double, _P, _P, _P, _P]),
+    "wsm_quantize_batch_stages": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_double, _P, _P, _P,
+                                            C.c_uint, _P]),
     "wsm_launch_shape": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                    C.POINTER(C.c_int)]),
     "wsm_set_launch_shape": (C.c_int, [_P, C.c_int]),
@@ -471,18 +473,23 @@ def _seeds(seeds, n):
     return (C.c_uint64 * max(n, 1))(*[int(x) & (2**64 - 1) for x in seeds])
 
 
+STAGE_REDUCE, STAGE_INIT, STAGE_ITERATE, STAGE_MAP, STAGE_DISTORTION = 1, 2, 4, 8, 16
+STAGE_ALL = 31
+
+
 def wsm_quantize_batch(h: Handle, items, n_items: int, seeds, max_iter: int, eps: float,
                        d_n_unique: torch.Tensor | None = None, d_iters: torch.Tensor | None = None,
-                       d_mse: torch.Tensor | None = None, stream=None):
-    """Enqueue the whole path for a batch (items: a pipeline_items array);
-    nothing is synchronised, so a CUDA graph can capture it."""
+                       d_mse: torch.Tensor | None = None, stages: int = STAGE_ALL, stream=None):
+    """Enqueue the path (or the given stages of it) for a batch (items: a
+    pipeline_items array); nothing is synchronised, so a CUDA graph can
+    capture it."""
     sd = seeds if isinstance(seeds, C.Array) else _seeds(seeds, n_items)
-    _check(lib().wsm_quantize_batch(h.ptr, C.cast(items, C.c_void_p), n_items,
-                                    C.cast(sd, C.c_void_p), int(max_iter), float(eps),
-                                    _dev(d_n_unique, torch.int64, "d_n_unique", n_items),
-                                    _dev(d_iters, torch.int32, "d_iters", n_items),
-                                    _dev(d_mse, torch.float64, "d_mse", n_items),
-                                    _stream(stream)))
+    _check(lib().wsm_quantize_batch_stages(h.ptr, C.cast(items, C.c_void_p), n_items,
+                                           C.cast(sd, C.c_void_p), int(max_iter), float(eps),
+                                           _dev(d_n_unique, torch.int64, "d_n_unique", n_items),
+                                           _dev(d_iters, torch.int32, "d_iters", n_items),
+                                           _dev(d_mse, torch.float64, "d_mse", n_items),
+                                           int(stages), _stream(stream)))
 
 
 def wsm_launch_shape(h: Handle, shape: int = -1) -> tuple[int, int, int, bool]:

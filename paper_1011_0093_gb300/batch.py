@@ -45,6 +45,7 @@ class BatchPlan:
         self._items = N.pipeline_items(self.images)
         self._seeds = N._seeds(list(seeds), self.n_items)
         self.graph = None
+        self.graphs = []
 
     def load(self, images, non_blocking: bool = True):
         """Copy new pixels (uint8 [H, W, C] tensors, host or device) into the
@@ -52,10 +53,12 @@ class BatchPlan:
         for dst, src in zip((im["rgb"] for im in self.images), images):
             dst.copy_(torch.as_tensor(src), non_blocking=non_blocking)
 
-    def run(self, stream=None):
-        """Enqueue unique colors -> init -> iterations -> mapping -> MSE."""
+    def run(self, stages: int = N.STAGE_ALL, stream=None):
+        """Enqueue unique colors -> init -> iterations -> mapping -> MSE (or
+        the given stages, on the state the earlier ones left)."""
         N.wsm_quantize_batch(self.handle, self._items, self.n_items, self._seeds, self.max_iter,
-                             self.eps, self.n_unique, self.iters, self.mse, stream=stream)
+                             self.eps, self.n_unique, self.iters, self.mse, stages=stages,
+                             stream=stream)
 
     def tune(self, repeats: int = 2):
         """Pick the persistent kernel's launch shape on the loaded images."""
@@ -67,24 +70,32 @@ class BatchPlan:
         launch (after tune(): of the Sort-Means iterations)."""
         return N.wsm_batch_stats(self.handle, self.n_items)
 
-    def capture(self):
-        """Capture run() into a CUDA graph (after one eager run to warm up)."""
+    def capture(self, parts=(N.STAGE_ALL,)):
+        """Capture run() into CUDA graphs, one per entry of `parts` (stage
+        bits, replayed in that order by replay()), after one eager run."""
         side = torch.cuda.Stream(device=self.device)
         side.wait_stream(torch.cuda.current_stream(self.device))
         with torch.cuda.stream(side):
-            self.run()
+            for stages in parts:
+                self.run(stages)
         torch.cuda.current_stream(self.device).wait_stream(side)
         torch.cuda.synchronize(self.device)
         N.wsm_sync_status(self.handle)
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph):
-            self.run()
-        return self.graph
+        self.graphs = []
+        for stages in parts:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self.run(stages)
+            self.graphs.append(g)
+        self.graph = self.graphs[0]
+        return self.graphs
 
-    def replay(self):
+    def replay(self, part: int | None = None):
+        """Replay the captured graphs in order (or only graph `part`)."""
         if self.graph is None:
             raise RuntimeError("capture() first")
-        self.graph.replay()
+        for g in (self.graphs if part is None else [self.graphs[part]]):
+            g.replay()
 
     def sync(self):
         """Wait for the work and raise any device-side error (e.g. an image

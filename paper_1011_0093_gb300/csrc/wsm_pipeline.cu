@@ -54,27 +54,39 @@ static int check_batch(wsm_handle* h, const wsm_item* items, int n_items, const 
 
 using namespace wsm;
 
+extern "C" int wsm_quantize_batch_stages(wsm_handle* h, const wsm_item* items, int n_items,
+                                         const uint64_t* seeds, int max_iter, double eps,
+                                         int64_t* d_n_unique, int* d_iters, double* d_mse,
+                                         unsigned stages, wsm_stream stream) {
+    int rc = check_batch(h, items, n_items, seeds, max_iter);
+    if (rc != WSM_OK) return rc;
+    if (stages & ~(unsigned)WSM_STAGE_ALL) return fail(WSM_E_INVAL, "unknown stage bits");
+    if (n_items == 0) return WSM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (stages & WSM_STAGE_REDUCE) rc = reduce_items(h, items, n_items, s);
+    if (rc == WSM_OK && (stages & WSM_STAGE_INIT)) rc = init_items_dev(h, items, n_items, seeds, s);
+    if (rc == WSM_OK && (stages & WSM_STAGE_ITERATE)) {
+        rc = iterate_items(h, items, n_items, max_iter, eps, h->batch_nu, s);
+        if (rc == WSM_OK && (d_n_unique || d_iters)) {
+            // before the mapping launch resets the slots' counters
+            k_outputs<<<(n_items + 255) / 256, 256, 0, s>>>(n_items, h->batch_nu, h->slot_ctrl,
+                                                             d_n_unique, d_iters);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) rc = cuda_fail(e, "output launch");
+        }
+    }
+    if (rc == WSM_OK && (stages & WSM_STAGE_MAP)) rc = map_items(h, items, n_items, h->batch_nu, s);
+    if (rc == WSM_OK && (stages & WSM_STAGE_DISTORTION))
+        rc = distortion_items(h, items, n_items, d_mse, h->batch_nu, s);
+    return rc;
+}
+
 extern "C" int wsm_quantize_batch(wsm_handle* h, const wsm_item* items, int n_items,
                                   const uint64_t* seeds, int max_iter, double eps,
                                   int64_t* d_n_unique, int* d_iters, double* d_mse,
                                   wsm_stream stream) {
-    int rc = check_batch(h, items, n_items, seeds, max_iter);
-    if (rc != WSM_OK) return rc;
-    if (n_items == 0) return WSM_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    rc = reduce_items(h, items, n_items, s);
-    if (rc == WSM_OK) rc = init_items_dev(h, items, n_items, seeds, s);
-    if (rc == WSM_OK) rc = iterate_items(h, items, n_items, max_iter, eps, h->batch_nu, s);
-    if (rc != WSM_OK) return rc;
-    if (d_n_unique || d_iters) {   // before the mapping launch resets the slots' counters
-        k_outputs<<<(n_items + 255) / 256, 256, 0, s>>>(n_items, h->batch_nu, h->slot_ctrl,
-                                                         d_n_unique, d_iters);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "output launch");
-    }
-    rc = map_items(h, items, n_items, h->batch_nu, s);
-    if (rc == WSM_OK) rc = distortion_items(h, items, n_items, d_mse, h->batch_nu, s);
-    return rc;
+    return wsm_quantize_batch_stages(h, items, n_items, seeds, max_iter, eps, d_n_unique, d_iters,
+                                     d_mse, WSM_STAGE_ALL, stream);
 }
 
 extern "C" int wsm_batch_stats(wsm_handle* h, int n_items, int64_t* evaluated, int* iters,

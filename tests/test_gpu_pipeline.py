@@ -179,3 +179,30 @@ def test_an_image_with_fewer_colors_than_K_is_reported_and_skipped(wsm):
             assert torch.equal(got["centers"], ref["centers"])
             assert torch.equal(got["index"], ref["index"])
     assert plan.result(1)["n_unique"] == 1
+
+
+def test_stages_in_separate_calls_and_graphs_equal_one_call(wsm):
+    imgs, Ks = uneven_batch(7, seed0=2500)
+    seeds = [3 * q + 7 for q in range(len(imgs))]
+    whole = wsm.BatchPlan([i.shape for i in imgs], Ks, seeds, max_iter=10)
+    whole.load([torch.from_numpy(i) for i in imgs])
+    whole.run()
+    whole.sync()
+    parts = (wsm.STAGE_REDUCE | wsm.STAGE_INIT, wsm.STAGE_ITERATE,
+             wsm.STAGE_MAP | wsm.STAGE_DISTORTION)
+    split = wsm.BatchPlan([i.shape for i in imgs], Ks, seeds, max_iter=10)
+    split.load([torch.from_numpy(i) for i in imgs])
+    for stages in parts:
+        split.run(stages)
+    split.sync()
+    graphs = wsm.BatchPlan([i.shape for i in imgs], Ks, seeds, max_iter=10)
+    graphs.load([torch.from_numpy(i) for i in imgs])
+    graphs.capture(parts)
+    for q in range(3):
+        graphs.replay(q)
+    graphs.sync()
+    for q in range(len(imgs)):
+        a, b, c = whole.result(q), split.result(q), graphs.result(q)
+        for r in (b, c):
+            assert r["n_unique"] == a["n_unique"] and r["iters"] == a["iters"] and r["mse"] == a["mse"]
+            assert torch.equal(r["centers"], a["centers"]) and torch.equal(r["index"], a["index"])
