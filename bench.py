@@ -244,10 +244,16 @@ def run_gpu(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     plan = wsm.BatchPlan([im.shape for im in images], K_PALETTE, seeds, max_iter=ITERS)
     plan.load(h_imgs)
-    # the iterations, once on their own: distances evaluated per image (the
-    # same every step: same inputs) for the roofline
+    # the iterations, once on their own, for the roofline (the same every step:
+    # same inputs): the distances Algorithm 2's visits evaluate (the work
+    # counted per unit), then the distances the launch computes with the
+    # first pass started at the grid candidates (the default)
+    wsm.wsm_set_first_pass_start(plan.handle, False)
     plan.run(wsm.STAGE_REDUCE | wsm.STAGE_INIT | wsm.STAGE_ITERATE)
     evaluated, _ = plan.stats()
+    wsm.wsm_set_first_pass_start(plan.handle, True)
+    plan.run(wsm.STAGE_REDUCE | wsm.STAGE_INIT | wsm.STAGE_ITERATE)
+    executed, _ = plan.stats()
     # one step = three captured graphs replayed back to back: a1-a2, a3-a6
     # (one persistent launch over the 8 images), a7-a8; events between them
     # time the iterations inside the timed region
@@ -368,6 +374,7 @@ def run_gpu(args):
                                       f"({pk_kind} max clock)",
                          "launch_ms": sum(it_ms) / len(it_ms),
                          "flop_per_launch": 8.0 * sum(evaluated),
+                         "flop_per_launch_executed": 8.0 * sum(executed),
                          "timed": "the iterate graph (plan kernel, counter clears, persistent "
                                   "launch, output copy) between CUDA events in every step"},
             "cpu_baseline": cpu,

@@ -357,6 +357,20 @@ WSM_API int wsm_launch_shape(wsm_handle* h, int shape, int* threads, int* blocks
                              int* resident);
 WSM_API int wsm_set_launch_shape(wsm_handle* h, int shape);
 
+/* How the first pass of each iterate launch searches (no counterpart in the
+ * paper: it changes the work, not the outcome).  candidate = 1 (default):
+ * each color's search starts at the center nearest to its 16^3 cell of the
+ * RGB cube (found once per launch) and visits that center's row up to the
+ * triangle-inequality bound; the winner is the one Algorithm 2's visit of
+ * row m[i] would keep (equal distances: the latest in that row), and the
+ * visit of row m[i] itself is made whenever that winner would not be on it.
+ * The memberships, sums and SSE are those of Algorithm 2; far fewer
+ * distances are computed when the memberships are far off (all 0 after the
+ * initialisation).  candidate = 0: every pass visits row m[i] as Algorithm 2
+ * does (the distance counts of wsm_iterate_stats are then Algorithm 2's).
+ * Errors: WSM_E_STATE (wrong device). */
+WSM_API int wsm_set_first_pass_start(wsm_handle* h, int candidate);
+
 /* Limits every persistent launch of the handle to `blocks` blocks (0: the
  * whole co-resident grid of its shape), so that several handles on several
  * streams can run their persistent launches side by side on one GPU.

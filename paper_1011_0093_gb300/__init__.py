@@ -17,7 +17,7 @@ from ._native import (MAX_K, MAX_PIXELS, Handle, WsmError, lib, wsm_distortion,
                       wsm_map_batch, wsm_reduce, wsm_reduce_batch, wsm_reserve_batch,
                       wsm_sync_status, wsm_quantize_batch, wsm_autotune_batch,
                       wsm_launch_shape, wsm_set_launch_shape, wsm_batch_stats,
-                      wsm_set_grid_limit, pipeline_items, STAGE_REDUCE, STAGE_INIT,
+                      wsm_set_grid_limit, wsm_set_first_pass_start, pipeline_items, STAGE_REDUCE, STAGE_INIT,
                       STAGE_ITERATE, STAGE_MAP, STAGE_DISTORTION, STAGE_ALL)
 from .batch import BatchPlan
 from .serve import Server
@@ -29,7 +29,7 @@ __all__ = ["MAX_K", "MAX_PIXELS", "Handle", "WsmError", "lib", "wsm_reduce", "ws
            "wsm_map_batch", "wsm_reserve_batch", "wsm_reduce_batch", "wsm_init_batch",
            "wsm_distortion_batch", "wsm_distortion_fwd", "wsm_distortion_bwd",
            "WeightedDistortion", "weighted_distortion", "wsm_quantize_batch",
-           "wsm_autotune_batch", "wsm_launch_shape", "wsm_set_launch_shape", "wsm_batch_stats", "wsm_set_grid_limit", "pipeline_items", "STAGE_REDUCE", "STAGE_INIT",
+           "wsm_autotune_batch", "wsm_launch_shape", "wsm_set_launch_shape", "wsm_batch_stats", "wsm_set_grid_limit", "wsm_set_first_pass_start", "pipeline_items", "STAGE_REDUCE", "STAGE_INIT",
            "STAGE_ITERATE", "STAGE_MAP", "STAGE_DISTORTION", "STAGE_ALL",
            "BatchPlan", "Server", "wsm_map", "wsm_distortion", "wsm_sync_status",
            "Quantized", "quantize", "quantize_batch"]

@@ -90,6 +90,7 @@ SIGNATURES = {
     "wsm_set_launch_shape": (C.c_int, [_P, C.c_int]),
     "wsm_batch_stats": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "wsm_set_grid_limit": (C.c_int, [_P, C.c_int]),
+    "wsm_set_first_pass_start": (C.c_int, [_P, C.c_int]),
     "wsm_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(ServerConfig)]),
     "wsm_server_submit": (C.c_int, [_P, C.POINTER(Request), C.POINTER(C.c_uint64)]),
     "wsm_server_wait": (C.c_int, [_P, C.c_uint64, C.c_double, C.POINTER(Result)]),
@@ -528,3 +529,7 @@ def wsm_batch_stats(h: Handle, n_items: int, stream=None) -> tuple[list[int], li
 
 def wsm_set_grid_limit(h: Handle, blocks: int):
     _check(lib().wsm_set_grid_limit(h.ptr, int(blocks)))
+
+
+def wsm_set_first_pass_start(h: Handle, candidate: bool):
+    _check(lib().wsm_set_first_pass_start(h.ptr, int(bool(candidate))))

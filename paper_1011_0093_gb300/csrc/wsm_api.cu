@@ -215,7 +215,7 @@ int iterate_kernel_setup(wsm_handle* h);   // wsm_iterate.cu
 void free_slots(wsm_handle* h) {
     void* ptrs[] = {h->tab,   h->tab_nb, h->sums,      h->sums64,   h->acc,       h->trace,
                     h->lut,   h->slot_ctrl, h->hist,   h->bitmap,   h->blk_total, h->batch_nu,
-                    h->batch_mse, h->pick, h->plan};
+                    h->batch_mse, h->pick, h->plan, h->grid};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     void* host_ptrs[] = {h->host_nu, h->host_mse, h->host_pick};
@@ -228,6 +228,7 @@ void free_slots(wsm_handle* h) {
     h->batch_mse = nullptr;
     h->pick = nullptr;
     h->plan = nullptr;
+    h->grid = nullptr;
     h->host_nu = nullptr;
     h->host_mse = nullptr;
     h->host_pick = nullptr;
@@ -268,6 +269,7 @@ int alloc_slots(wsm_handle* h, int slots) {
         {(void**)&h->batch_mse, sizeof(double) * n},
         {(void**)&h->pick, sizeof(uint32_t) * (size_t)h->max_K * n},
         {(void**)&h->plan, sizeof(int) * (n / kMaxBatch + 1) * (kMaxBatch + 1)},
+        {(void**)&h->grid, (size_t)kGridCells * n},
     };
     for (auto& a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.bytes);

@@ -34,6 +34,7 @@ constexpr int kCopies = 8;                   // replicas of the global accumulat
 constexpr int kChunk = 32;                   // colors per warp chunk (one per lane)
 constexpr int kMaxBatch = 48;                // images per persistent launch
 constexpr int kReduceSlots = 16;             // images per unique-color reduction launch
+constexpr int kGridCells = 4096;             // 16^3 cells of the first pass's candidate grid
 
 // A launch shape of the persistent sort-means kernel.
 struct IterShape {
@@ -67,6 +68,7 @@ struct wsm_handle {
     int64_t max_unique = 0;
     int iter_shape = 0;          // index into kIterShapes used by the persistent launches
     int grid_limit = 0;          // > 0: at most this many blocks per persistent launch
+    bool cand_start = true;      // see wsm_set_first_pass_start
     bool shape_ok[wsm::kNumIterShapes] = {};   // shapes whose blocks can all be resident
     // scratch (device)
     double* mse_part = nullptr;  // [1024] block partials + [1] result
@@ -91,6 +93,7 @@ struct wsm_handle {
     unsigned long long* acc = nullptr;     // [slots][4 max_K] S_k (3) and W_k of the last pass
     double* trace = nullptr;     // [slots][kMaxTrace]
     uint8_t* lut = nullptr;      // [slots][2^24] color -> label
+    uint8_t* grid = nullptr;     // [slots][kGridCells] candidate center per RGB cell
     wsm::Ctrl* slot_ctrl = nullptr;  // [slots] barrier counter, iterations, distances
     int64_t* batch_nu = nullptr;     // [slots] N' of each image of the last wsm_reduce_batch
     double* batch_mse = nullptr;     // [slots] MSE of each image of the last wsm_distortion_batch

@@ -71,6 +71,7 @@ struct Scratch {
     unsigned long long* acc;   // [4 max_K] cluster sums of the last pass
     double* trace;             // [kMaxTrace]
     uint8_t* lut;              // [2^24] color -> label (map mode)
+    uint8_t* grid;             // [kGridCells] a nearby center for each 16^3 cell of the RGB cube
     Ctrl* ctrl;                // barrier counter, iterations, distances
     int max_K;
 };
@@ -84,6 +85,7 @@ struct BatchParams {
     const int64_t* n_dev;      // if set, image i has n_dev[item[i].slot] colors (written by an
                                //   earlier kernel) and the split is first_dev (k_plan)
     const int* first_dev;
+    int cand_start;            // first pass of an iterate launch starts at the grid candidate
     int first_blk[kMaxBatch + 1];  // image i owns blocks [first_blk[i], first_blk[i+1])
     ItemDesc item[kMaxBatch];
 };
@@ -194,6 +196,88 @@ __global__ void k_plan(const __grid_constant__ BatchParams P, int threads, int g
     split_groups(want, P.n_items, grid, first_dev);
 }
 
+// Cell of the 16^3 grid over the RGB cube that holds color 0x00RRGGBB.
+__device__ __forceinline__ int grid_cell(uint32_t col) {
+    return (int)(((col >> 12) & 0xF00u) | ((col >> 8) & 0xF0u) | ((col >> 4) & 0xFu));
+}
+
+// Sort key of center t in row p, exactly as build_rows computes it.
+__device__ __forceinline__ unsigned long long key_in_row(const float4* s_c, int p, int t) {
+    const float4 a = s_c[p], c = s_c[t];
+    return row_key(sq3(a.x, a.y, a.z, c.x, c.y, c.z), t, p);
+}
+
+struct CandResult {
+    int best;      // the winner, or -1 if row p must be visited after all
+    float mn;      // its squared distance
+    int visits;    // distances computed
+};
+
+// The first-pass search of color x (membership p, prev = ||x - c_p||^2) from
+// the grid candidate q != p: visits row q up to the bound dq = ||x - c_q||^2
+// (no center past it is nearer than c_q), keeping the nearest center with
+// ties to the one latest in row p, and returns it if Algorithm 2's visit of
+// row p would meet it (d[p][t] / 4 < prev, or t = p).
+__device__ __forceinline__ CandResult candidate_search(float x, float y, float z, int p, int q,
+                                                    float prev, int K, const float4* s_c,
+                                                    const float4* tab, const uint8_t* tab_nb) {
+    const float4 cq = s_c[q];
+    const float dq = sq3(x, y, z, cq.x, cq.y, cq.z);
+    const float4* rq = tab + (size_t)q * K;
+    const uint8_t* nq = tab_nb + (size_t)q * K;
+    int bpos = -1;                 // the best so far: c_p (-1), c_q (0) or entry bpos of row q
+    float bmn = prev;
+    if (dq <= prev) {              // c_q is later than c_p in row p
+        bpos = 0;
+        bmn = dq;
+    }
+    int v = 2;
+    const auto center_at = [&](int pos) { return pos < 0 ? p : pos == 0 ? q : (int)nq[pos]; };
+    const auto visit = [&](const float4& e, int pos) {
+        const float d = sq3(x, y, z, e.y, e.z, e.w);
+        ++v;
+        if (d < bmn) {
+            bmn = d;
+            bpos = pos;
+        } else if (d == bmn &&
+                   key_in_row(s_c, p, center_at(pos)) > key_in_row(s_c, p, center_at(bpos))) {
+            bpos = pos;
+        }
+    };
+    int j = 1;
+    bool go = true;
+    for (; go && j + 3 < K; j += 4) {
+        const float4 e0 = rq[j], e1 = rq[j + 1], e2 = rq[j + 2], e3 = rq[j + 3];
+        if (e3.x <= dq) {
+            visit(e0, j);
+            visit(e1, j + 1);
+            visit(e2, j + 2);
+            visit(e3, j + 3);
+        } else {
+            go = false;
+            if (e0.x <= dq) {
+                visit(e0, j);
+                if (e1.x <= dq) {
+                    visit(e1, j + 1);
+                    if (e2.x <= dq) visit(e2, j + 2);
+                }
+            }
+        }
+    }
+    for (; go && j < K; ++j) {
+        const float4 e = rq[j];
+        if (e.x > dq) break;
+        visit(e, j);
+    }
+    const int best = center_at(bpos);
+    const float4 cp = s_c[p], cb = s_c[best];
+    CandResult r;
+    r.best = (best == p || sq3(cp.x, cp.y, cp.z, cb.x, cb.y, cb.z) * 0.25f < prev) ? best : -1;
+    r.mn = bmn;
+    r.visits = v;
+    return r;
+}
+
 // One visited entry: distance, and the update with the later entry winning ties.
 #define WSM_VISIT(e, jj)                                        \
     {                                                           \
@@ -203,6 +287,147 @@ __global__ void k_plan(const __grid_constant__ BatchParams P, int threads, int g
             mpos = (jj);                                        \
         }                                                       \
     }
+
+// One assignment pass over an image's colors by one warp (phase B of
+// k_sortmeans): the warp's chunks of 32 colors, one color per lane, each
+// color's pruned visit of its row, and the per-block sums.  kCand: the first
+// pass of an iterate launch, whose search starts at the grid candidate.
+template <bool kMap, bool kCand>
+__device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K, int G, int b,
+                                            int WPB, int lane, int wid, unsigned* ticket,
+                                            const float4* s_c, unsigned* s_acc, const float4* tab,
+                                            const uint8_t* tab_nb, const uint8_t* grid, uint8_t* lut,
+                                            unsigned long long& sse_fx, unsigned long long& ev,
+                                            unsigned long long& npix, unsigned long long& nonzero,
+                                            bool& bad) {
+    // Chunks: warp w of block b starts with chunk b * WPB + w, then takes
+    // chunks G * WPB + t in the order of the tickets t it draws from the
+    // slot's counter (each ticket drawn one chunk ahead), so the warps of
+    // the group finish together whatever the cost of their colors.
+    int64_t cur = ((int64_t)b * WPB + wid) * kChunk;
+    int64_t nxt = n;
+    {
+        unsigned t = 0;
+        if (lane == 0 && cur < n) t = atomicAdd(ticket, 1u);
+        t = __shfl_sync(0xFFFFFFFFu, t, 0);
+        if (cur < n) nxt = ((int64_t)G * WPB + t) * kChunk;
+    }
+    uint32_t col_n = 0, cnt_n = 0;
+    int lab_n = 0;
+    if (cur + lane < n) {
+        col_n = __ldg(I.colors + cur + lane);
+        lab_n = I.labels[cur + lane];
+        if (!kMap) cnt_n = __ldg(I.counts + cur + lane);
+    }
+    while (cur < n) {
+        const int64_t i = cur + lane;
+        const bool active = i < n;
+        const uint32_t col = col_n;
+        const unsigned cnt = cnt_n;
+        const int p0 = lab_n;
+        unsigned t_after = 0;
+        if (nxt < n) {
+            if (nxt + lane < n) {
+                col_n = __ldg(I.colors + nxt + lane);
+                lab_n = I.labels[nxt + lane];
+                if (!kMap) cnt_n = __ldg(I.counts + nxt + lane);
+            }
+            if (lane == 0) t_after = atomicAdd(ticket, 1u);   // used after this chunk
+        }
+        int p = p0;
+        if (p >= K) {                          // invalid input membership
+            bad = true;
+            p = 0;
+        }
+        const float x = (float)((col >> 16) & 255u);
+        const float y = (float)((col >> 8) & 255u);
+        const float z = (float)(col & 255u);
+        const float4 cp = s_c[p];
+        const float prev = sq3(x, y, z, cp.x, cp.y, cp.z);
+        float mn = prev;
+        int mpos = 0;
+        int j = 1;
+        int lab = p;
+        bool scan_p = active;
+        if (kCand && active) {
+            // First pass of the launch, where the memberships may be far
+            // off (all 0 after the initialisation): the same outcome as the
+            // visit of row p from a nearer start.  With q the grid
+            // candidate and dq = ||x - c_q||^2, every center at least as
+            // near as c_q has d[q][t] <= 4 dq, so visiting row q up to that
+            // bound meets every nearest center; among equal distances the
+            // one latest in row p wins (the later visit wins in row p).
+            // If the winner would not be visited in row p (d[p][t] >=
+            // 4 prev, which the triangle inequality rules out but for
+            // rounding at the bound), row p is visited as usual.
+            const int q = grid[grid_cell(col)];
+            if (q != p) {
+                const CandResult r = candidate_search(x, y, z, p, q, prev, K, s_c, tab, tab_nb);
+                if (r.best >= 0) {
+                    scan_p = false;
+                    lab = r.best;
+                    mn = r.mn;
+                    ev += (unsigned long long)r.visits;
+                }
+            }
+        }
+        if (scan_p) {
+            const float4* row = tab + (size_t)p * K;
+            bool more = true;
+            for (; more && j + 3 < K; j += 4) {
+                const float4 e0 = row[j], e1 = row[j + 1], e2 = row[j + 2], e3 = row[j + 3];
+                if (e3.x < prev) {
+                    WSM_VISIT(e0, j);
+                    WSM_VISIT(e1, j + 1);
+                    WSM_VISIT(e2, j + 2);
+                    WSM_VISIT(e3, j + 3);
+                } else {
+                    more = false;
+                    if (e0.x < prev) {
+                        WSM_VISIT(e0, j);
+                        if (e1.x < prev) {
+                            WSM_VISIT(e1, j + 1);
+                            if (e2.x < prev) {
+                                WSM_VISIT(e2, j + 2);
+                                j += 3;
+                            } else {
+                                j += 2;
+                            }
+                        } else {
+                            j += 1;
+                        }
+                    }
+                    break;
+                }
+            }
+            for (; more && j < K; ++j) {
+                const float4 e = row[j];
+                if (e.x >= prev) break;        // d[p][t] >= 4 prev_dist: stop
+                WSM_VISIT(e, j);
+            }
+            ev += (unsigned long long)j;       // c_p plus the j - 1 visited centers
+            lab = mpos ? tab_nb[(size_t)p * K + mpos] : p;
+        }
+        if (active) {
+            if (lab != p0) I.labels[i] = (uint8_t)lab;
+            if (kMap) {
+                lut[col & 0xFFFFFFu] = (uint8_t)lab;
+            } else {
+                atomicAdd(s_acc + 4 * lab + 0, cnt * ((col >> 16) & 255u));
+                atomicAdd(s_acc + 4 * lab + 1, cnt * ((col >> 8) & 255u));
+                atomicAdd(s_acc + 4 * lab + 2, cnt * (col & 255u));
+                atomicAdd(s_acc + 4 * lab + 3, cnt);
+                atomicMax(s_acc + 4 * K + lab, __float_as_uint(mn));
+                sse_fx += sse_fixed(cnt, mn);
+                npix += cnt;
+                nonzero += mn > 0.f;
+            }
+        }
+        const unsigned t = __shfl_sync(0xFFFFFFFFu, t_after, 0);
+        cur = nxt;
+        nxt = cur < n ? ((int64_t)G * WPB + t) * kChunk : n;
+    }
+}
 
 template <bool kMap, int kThreads>
 __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sortmeans(const __grid_constant__ BatchParams P) {
@@ -248,6 +473,30 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sortmeans(const _
     for (int j = tid; j < 5 * K; j += T) s_acc[j] = 0u;
     __syncthreads();
 
+    // The candidate grid (iterations only): for every 16^3 cell of the RGB
+    // cube the center nearest to the cell's middle, where the first pass of
+    // the launch starts each color's search (see there).
+    uint8_t* const grid = P.sc.grid + (size_t)I.slot * kGridCells;
+    const bool cand = !kMap && P.cand_start;
+    if (cand) {
+        for (int c = b * T + tid; c < kGridCells; c += G * T) {
+            const float gx = (float)((c >> 8) * 16 + 8), gy = (float)(((c >> 4) & 15) * 16 + 8),
+                        gz = (float)((c & 15) * 16 + 8);
+            float bd = __int_as_float(0x7f800000);
+            int bt = 0;
+            for (int k = 0; k < K; ++k) {
+                const float4 ck = s_c[k];
+                const float d = sq3(gx, gy, gz, ck.x, ck.y, ck.z);
+                if (d < bd) {
+                    bd = d;
+                    bt = k;
+                }
+            }
+            grid[c] = (uint8_t)bt;
+        }
+        if (!grid_sync(&ctrl->bar_count, P.status, G)) return;
+    }
+
     // Colors of this block: chunks of kChunk, one per lane, warp w of block b
     // takes chunks b * WPB + w + m * G * WPB.
     const int64_t first = ((int64_t)b * WPB + wid) * kChunk;
@@ -265,10 +514,18 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sortmeans(const _
                     bad = true;
                     p = 0;
                 }
+                const float x = (float)((col >> 16) & 255u), y = (float)((col >> 8) & 255u),
+                            z = (float)(col & 255u);
                 const float4 cp = s_c[p];
-                const float prev = sq3((float)((col >> 16) & 255u), (float)((col >> 8) & 255u),
-                                       (float)(col & 255u), cp.x, cp.y, cp.z);
+                const float prev = sq3(x, y, z, cp.x, cp.y, cp.z);
                 atomicMax(s_acc + 4 * K + p, __float_as_uint(prev));
+                if (cand) {                        // the first pass also reads row q
+                    const int q = grid[grid_cell(col)];
+                    if (q != p) {
+                        const float4 cq = s_c[q];
+                        atomicMax(s_acc + 4 * K + q, __float_as_uint(sq3(x, y, z, cq.x, cq.y, cq.z)));
+                    }
+                }
             }
         }
         if (bad) atomicOr(P.status, ST_BAD_LABEL);
@@ -298,107 +555,17 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sortmeans(const _
         __syncthreads();
         unsigned long long sse_fx = 0, ev = 0, npix = 0, nonzero = 0;
         bool bad = false;
-        // Chunks: warp w of block b starts with chunk b * WPB + w, then takes
-        // chunks G * WPB + t in the order of the tickets t it draws from the
-        // slot's counter (each ticket drawn one chunk ahead), so the warps of
-        // the group finish together whatever the cost of their colors.
         unsigned* const ticket = &ctrl->ticket[buf];
-        int64_t cur = ((int64_t)b * WPB + wid) * kChunk;
-        int64_t nxt = n;
-        {
-            unsigned t = 0;
-            if (lane == 0 && cur < n) t = atomicAdd(ticket, 1u);
-            t = __shfl_sync(0xFFFFFFFFu, t, 0);
-            if (cur < n) nxt = ((int64_t)G * WPB + t) * kChunk;
-        }
-        uint32_t col_n = 0, cnt_n = 0;
-        int lab_n = 0;
-        if (cur + lane < n) {
-            col_n = __ldg(I.colors + cur + lane);
-            lab_n = I.labels[cur + lane];
-            if (!kMap) cnt_n = __ldg(I.counts + cur + lane);
-        }
-        while (cur < n) {
-            const int64_t i = cur + lane;
-            const bool active = i < n;
-            const uint32_t col = col_n;
-            const unsigned cnt = cnt_n;
-            const int p0 = lab_n;
-            unsigned t_after = 0;
-            if (nxt < n) {
-                if (nxt + lane < n) {
-                    col_n = __ldg(I.colors + nxt + lane);
-                    lab_n = I.labels[nxt + lane];
-                    if (!kMap) cnt_n = __ldg(I.counts + nxt + lane);
-                }
-                if (lane == 0) t_after = atomicAdd(ticket, 1u);   // used after this chunk
-            }
-            int p = p0;
-            if (p >= K) {                          // invalid input membership
-                bad = true;
-                p = 0;
-            }
-            const float x = (float)((col >> 16) & 255u);
-            const float y = (float)((col >> 8) & 255u);
-            const float z = (float)(col & 255u);
-            const float4 cp = s_c[p];
-            const float prev = sq3(x, y, z, cp.x, cp.y, cp.z);
-            float mn = prev;
-            int mpos = 0;
-            int j = 1;
-            if (active) {
-                const float4* row = tab + (size_t)p * K;
-                bool more = true;
-                for (; more && j + 3 < K; j += 4) {
-                    const float4 e0 = row[j], e1 = row[j + 1], e2 = row[j + 2], e3 = row[j + 3];
-                    if (e3.x < prev) {
-                        WSM_VISIT(e0, j);
-                        WSM_VISIT(e1, j + 1);
-                        WSM_VISIT(e2, j + 2);
-                        WSM_VISIT(e3, j + 3);
-                    } else {
-                        more = false;
-                        if (e0.x < prev) {
-                            WSM_VISIT(e0, j);
-                            if (e1.x < prev) {
-                                WSM_VISIT(e1, j + 1);
-                                if (e2.x < prev) {
-                                    WSM_VISIT(e2, j + 2);
-                                    j += 3;
-                                } else {
-                                    j += 2;
-                                }
-                            } else {
-                                j += 1;
-                            }
-                        }
-                        break;
-                    }
-                }
-                for (; more && j < K; ++j) {
-                    const float4 e = row[j];
-                    if (e.x >= prev) break;        // d[p][t] >= 4 prev_dist: stop
-                    WSM_VISIT(e, j);
-                }
-                ev += (unsigned long long)j;       // c_p plus the j - 1 visited centers
-                const int lab = mpos ? tab_nb[(size_t)p * K + mpos] : p;
-                if (lab != p0) I.labels[i] = (uint8_t)lab;
-                if (kMap) {
-                    lut[col & 0xFFFFFFu] = (uint8_t)lab;
-                } else {
-                    atomicAdd(s_acc + 4 * lab + 0, cnt * ((col >> 16) & 255u));
-                    atomicAdd(s_acc + 4 * lab + 1, cnt * ((col >> 8) & 255u));
-                    atomicAdd(s_acc + 4 * lab + 2, cnt * (col & 255u));
-                    atomicAdd(s_acc + 4 * lab + 3, cnt);
-                    atomicMax(s_acc + 4 * K + lab, __float_as_uint(mn));
-                    sse_fx += sse_fixed(cnt, mn);
-                    npix += cnt;
-                    nonzero += mn > 0.f;
-                }
-            }
-            const unsigned t = __shfl_sync(0xFFFFFFFFu, t_after, 0);
-            cur = nxt;
-            nxt = cur < n ? ((int64_t)G * WPB + t) * kChunk : n;
+        if constexpr (!kMap) {
+            if (cand && it == 0)
+                assign_pass<false, true>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
+                                         tab_nb, grid, lut, sse_fx, ev, npix, nonzero, bad);
+            else
+                assign_pass<false, false>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
+                                          tab_nb, grid, lut, sse_fx, ev, npix, nonzero, bad);
+        } else {
+            assign_pass<true, false>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab, tab_nb,
+                                     grid, lut, sse_fx, ev, npix, nonzero, bad);
         }
         if (bad) atomicOr(P.status, ST_BAD_LABEL);
         sse_fx = warp_sum_u64(sse_fx);
@@ -590,6 +757,7 @@ static Scratch handle_scratch(wsm_handle* h) {
     sc.acc = h->acc;
     sc.trace = h->trace;
     sc.lut = h->lut;
+    sc.grid = h->grid;
     sc.ctrl = h->slot_ctrl;
     sc.max_K = h->max_K;
     return sc;
@@ -602,7 +770,7 @@ static Scratch handle_scratch(wsm_handle* h) {
 // launched; otherwise the host splits the blocks.
 int launch_batch(const Scratch& sc, unsigned* status, bool map_mode, const ItemDesc* items,
                  int n_items, int max_iter, double eps, int threads, int grid_cap,
-                 const int64_t* n_dev, int* first_dev, cudaStream_t s) {
+                 const int64_t* n_dev, int* first_dev, bool cand_start, cudaStream_t s) {
     BatchParams P;
     P.sc = sc;
     P.status = status;
@@ -611,6 +779,7 @@ int launch_batch(const Scratch& sc, unsigned* status, bool map_mode, const ItemD
     P.eps = eps;
     P.n_dev = n_dev;
     P.first_dev = n_dev ? first_dev : nullptr;
+    P.cand_start = cand_start ? 1 : 0;
     int64_t want[kMaxBatch];
     for (int i = 0; i < n_items; ++i) {
         P.item[i] = items[i];
@@ -656,7 +825,8 @@ int launch_sortmeans(wsm_handle* h, bool map_mode, const uint32_t* colors, const
     it.K = K;
     it.slot = 0;
     return launch_batch(handle_scratch(h), &h->ctrl->status, map_mode, &it, 1, max_iter, eps,
-                        kIterShapes[h->iter_shape].threads, iter_grid(h), nullptr, nullptr, s);
+                        kIterShapes[h->iter_shape].threads, iter_grid(h), nullptr, nullptr,
+                        h->cand_start, s);
 }
 
 // The final assignment of n_items images (slots slot0, slot0 + 1, ...) in
@@ -675,7 +845,7 @@ int launch_map_items(wsm_handle* h, const wsm_item* items, int n_items, int slot
     }
     return launch_batch(handle_scratch(h), &h->ctrl->status, true, d, n_items, 1, 0.0,
                         kIterShapes[h->iter_shape].threads, iter_grid(h), n_dev,
-                        h->plan + (size_t)(slot0 / kMaxBatch) * (kMaxBatch + 1), s);
+                        h->plan + (size_t)(slot0 / kMaxBatch) * (kMaxBatch + 1), false, s);
 }
 
 // The iterations of n_items images (item i in slot i), one persistent launch
@@ -697,7 +867,8 @@ int iterate_items(wsm_handle* h, const wsm_item* items, int n_items, int max_ite
         }
         int rc = launch_batch(handle_scratch(h), &h->ctrl->status, false, d, m, max_iter, eps,
                               kIterShapes[h->iter_shape].threads, iter_grid(h), n_dev,
-                              h->plan + (size_t)(i0 / kMaxBatch) * (kMaxBatch + 1), s);
+                              h->plan + (size_t)(i0 / kMaxBatch) * (kMaxBatch + 1),
+                              h->cand_start, s);
         if (rc != WSM_OK) return rc;
     }
     return WSM_OK;
@@ -838,7 +1009,8 @@ constexpr size_t kStaticOffSums = kStaticOffNb + kStaticNbBytes;
 constexpr size_t kStaticOffSums64 = kStaticOffSums + kStaticSumsBytes;
 constexpr size_t kStaticOffAcc = kStaticOffSums64 + kStaticSums64Bytes;
 constexpr size_t kStaticOffTrace = kStaticOffAcc + kStaticAccBytes;
-constexpr size_t kStaticOffCtrl = kStaticOffTrace + kStaticTraceBytes;
+constexpr size_t kStaticOffGrid = kStaticOffTrace + kStaticTraceBytes;
+constexpr size_t kStaticOffCtrl = kStaticOffGrid + kGridCells;
 constexpr size_t kStaticBytes = kStaticOffCtrl + 256;           // about 1.2 MiB in total
 static_assert(kStaticOffSums % 16 == 0 && kStaticOffCtrl % 16 == 0, "scratch alignment");
 
@@ -919,6 +1091,7 @@ extern "C" int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_c
     sc.acc = reinterpret_cast<unsigned long long*>(base + kStaticOffAcc);
     sc.trace = trace;
     sc.lut = nullptr;
+    sc.grid = base + kStaticOffGrid;
     sc.ctrl = ctrl;
     sc.max_K = kStaticMaxK;
     ItemDesc it;
@@ -930,7 +1103,7 @@ extern "C" int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_c
     it.K = K;
     it.slot = 0;
     rc = launch_batch(sc, &ctrl->status, false, &it, 1, max_iter, eps, kStaticThreads, st->grid,
-                      nullptr, nullptr, s);
+                      nullptr, nullptr, true, s);
     if (rc != WSM_OK) return rc;
     if (iters_done || sse_trace) {
         Ctrl host;

@@ -117,6 +117,13 @@ extern "C" int wsm_set_grid_limit(wsm_handle* h, int blocks) {
     return WSM_OK;
 }
 
+extern "C" int wsm_set_first_pass_start(wsm_handle* h, int candidate) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    h->cand_start = candidate != 0;
+    return WSM_OK;
+}
+
 extern "C" int wsm_set_launch_shape(wsm_handle* h, int shape) {
     int rc = check_handle(h);
     if (rc != WSM_OK) return rc;

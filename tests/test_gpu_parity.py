@@ -167,7 +167,7 @@ def test_init_all_colors_and_too_many(wsm, h):
 # ---- a3-a6: the Sort-Means iterations, teacher-forced ----------------------------
 
 def check_pass(colors, counts, c, lab, got_labels, got_centers, got_S, got_W, got_sse,
-               got_ev, it):
+               got_ev, it, paper_scan=True):
     """Compare one GPU pass with one oracle pass started from the same state
     (oracle centers c, memberships lab).  Returns the oracle's pass and the
     number of colors whose membership differs (each must be a near-tie)."""
@@ -185,7 +185,7 @@ def check_pass(colors, counts, c, lab, got_labels, got_centers, got_S, got_W, go
     expect = f32_centers(step["S"], step["W"], c)
     assert np.array_equal(got_centers[ok], expect[ok]), it
     assert np.abs(got_centers[ok] - step["centers"][ok]).max(initial=0.0) <= 1e-4
-    if it == 0 and not diff.any():       # integer centers: every FP32 distance is exact
+    if paper_scan and it == 0 and not diff.any():   # integer centers: exact FP32 distances
         assert got_ev == step["evaluated"]
     return step, int(diff.sum())
 
@@ -198,9 +198,12 @@ def gpu_pass(wsm, h, cd, nd, nu, K, centers, labels):
             ev)
 
 
-def teacher_forced(wsm, h, img, K, seed, iters):
+def teacher_forced(wsm, h, img, K, seed, iters, paper_scan=False):
     """Run `iters` oracle passes; before each, start the GPU from the
-    oracle's centers and memberships and compare one GPU pass with it."""
+    oracle's centers and memberships and compare one GPU pass with it.  Each
+    GPU pass is the first pass of its launch, so it uses the candidate start
+    unless paper_scan, which also checks the distance counts of Algorithm 2."""
+    wsm.wsm_set_first_pass_start(h, not paper_scan)
     colors, counts = oracle.unique(img)
     cd, nd = dev(colors), dev(counts)
     c, lab = oracle.init(colors, K, seed)
@@ -209,9 +212,10 @@ def teacher_forced(wsm, h, img, K, seed, iters):
         centers = dev(pad4(c.astype(np.float32)))
         labels = dev(lab.astype(np.uint8))
         out = gpu_pass(wsm, h, cd, nd, len(colors), K, centers, labels)
-        step, nflip = check_pass(colors, counts, c, lab, *out, it)
+        step, nflip = check_pass(colors, counts, c, lab, *out, it, paper_scan)
         flips += nflip
         c, lab = step["centers"], step["labels"]
+    wsm.wsm_set_first_pass_start(h, True)
     return flips
 
 
@@ -225,6 +229,13 @@ def test_iterations_teacher_forced_sweep512(wsm, h, s, K):
     teacher_forced(wsm, h, synth.sweep_512_one(s), K, 100 + s, 10)
 
 
+@pytest.mark.parametrize("img_fn,K,passes", [(synth.plain_256, 16, 12),
+                                             (lambda: synth.sweep_512_one(7), 256, 3)])
+def test_visits_and_counts_follow_algorithm_2_without_the_candidate_start(wsm, h, img_fn, K,
+                                                                          passes):
+    teacher_forced(wsm, h, img_fn(), K, 3, passes, paper_scan=True)
+
+
 def test_iterations_teacher_forced_ties(wsm, h):
     """Few levels per channel: exact distance ties everywhere, integer
     centers in the first pass, duplicate centers possible."""
@@ -232,6 +243,7 @@ def test_iterations_teacher_forced_ties(wsm, h):
         img = synth.tiny(40, 37, 50 + seed, 4)
         colors, _ = oracle.unique(img)
         teacher_forced(wsm, h, img, min(len(colors), 5 + 3 * seed), seed, 6)
+        teacher_forced(wsm, h, img, min(len(colors), 5 + 3 * seed), seed, 6, paper_scan=True)
 
 
 # ---- free-running: whole path vs the oracle's whole path --------------------------
@@ -268,7 +280,7 @@ def compare_whole_path(wsm, h, img, K, seed, max_iter, eps):
         out = gpu_pass(wsm, h, cd, nd, len(colors), K, centers, labels)
         gpu_trace.append(out[4])
         if diverged is None:
-            step, nflip = check_pass(colors, counts, c, lab, *out, it)
+            step, nflip = check_pass(colors, counts, c, lab, *out, it, paper_scan=False)
             if nflip:
                 diverged = it
             c, lab = step["centers"], step["labels"]
