@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_init_dev(const __grid_constant__ InitDe
     __shared__ uint32_t s_pick[WSM_MAX_K];
     __shared__ uint32_t s_sorted[WSM_MAX_K];
     const int i = blockIdx.x / kInitBlocks, j = blockIdx.x % kInitBlocks;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int64_t n = B.n_dev[i];
     const int K = B.K[i];
     if (n < K) {                                    // skipped: zero centers, flagged
@@ -160,19 +160,34 @@ __global__ void __launch_bounds__(256) k_init_dev(const __grid_constant__ InitDe
     for (int64_t q = (int64_t)j * blockDim.x + tid; q < n; q += (int64_t)kInitBlocks * blockDim.x)
         B.labels[i][q] = 0;
     if (j != 0) return;
+    // Floyd step r draws t_r = draw_r mod (top_r + 1), top_r = n - K + r, and
+    // takes t_r unless it is already taken, else top_r.  t_r is taken before
+    // step r exactly when an earlier draw had the same value (that value was
+    // taken then, as itself or already before), or when t_r = top_q for an
+    // earlier step q that took top_q.  The first test needs no order (all
+    // pairs at once); the second follows q < r, in one pass over the steps.
     for (int r = tid; r < K; r += blockDim.x)
         s_draw[r] = splitmix_draw(B.seed[i], (uint64_t)r) % (uint64_t)(n - K + r + 1);
     __syncthreads();
-    if (tid < 32) {
+    for (int r = tid; r < K; r += blockDim.x) {
+        const uint64_t t = s_draw[r];
+        bool seen = false;
+        for (int q = 0; q < r; ++q) seen |= s_draw[q] == t;
+        s_pick[r] = seen ? 1u : 0u;                  // for now: t_r equals an earlier draw
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int64_t base = n - K;
         for (int r = 0; r < K; ++r) {
-            const uint32_t t = (uint32_t)s_draw[r];
-            bool seen = false;
-            for (int q = lane; q < r; q += 32) seen |= s_pick[q] == t;
-            seen = __any_sync(0xFFFFFFFFu, seen);
-            if (lane == 0) s_pick[r] = seen ? (uint32_t)(n - K + r) : t;
-            __syncwarp();
+            const int64_t t = (int64_t)s_draw[r];
+            bool taken = s_pick[r] != 0;
+            if (!taken && t >= base && t - base < r) taken = s_pick[t - base] == 2u;
+            s_pick[r] = taken ? 2u : 3u;             // 2: took top_r, 3: took t_r
         }
     }
+    __syncthreads();
+    for (int r = tid; r < K; r += blockDim.x)
+        s_pick[r] = s_pick[r] == 2u ? (uint32_t)(n - K + r) : (uint32_t)s_draw[r];
     __syncthreads();
     for (int r = tid; r < K; r += blockDim.x) {     // the picks are distinct: rank = position
         const uint32_t v = s_pick[r];

@@ -79,14 +79,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_count(const __grid_consta
 }
 
 // Pass 2: each block finds its output offset from the totals of the blocks
-// before it, scans its words' bit counts into per-word output offsets, and
-// then emits (color, count) for every set bit: a warp takes one word at a
-// time, lane l handles bit l (so the 32 bins of a word are read and cleared
-// with one coalesced access), kEmitBatch words in flight per warp.  Output
-// order is ascending color order.
+// before it and scans its words into output offsets, listing the nonzero
+// words in order (one scan of the packed per-thread counts of set bits and
+// of nonzero words); then the warps take the listed words, kEmitBatch in
+// flight per warp, one word at a time with lane l handling bit l (so the 32
+// bins of a word are read and cleared with one coalesced access), and emit
+// (color, count) for every set bit.  Empty words cost nothing past the scan.
+// Output order is ascending color order.
 __global__ void __launch_bounds__(kScanThreads) k_scan_emit(const __grid_constant__ ReduceItems R) {
-    __shared__ uint32_t s_word[kScanWordsPerBlock];
-    __shared__ uint32_t s_off[kScanWordsPerBlock];
+    __shared__ uint32_t s_word[kScanWordsPerBlock];     // the block's nonzero words, in order
+    __shared__ uint32_t s_off[kScanWordsPerBlock];      // output offset of each (within the block)
+    __shared__ uint16_t s_idx[kScanWordsPerBlock];      // word index within the block
     __shared__ unsigned s_w[kScanThreads / 32];
     __shared__ unsigned long long s_base;
     const int item = blockIdx.x / kScanBlocks, b = blockIdx.x % kScanBlocks;
@@ -108,10 +111,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_emit(const __grid_constan
     uint4* wv = reinterpret_cast<uint4*>(bitmap + w0) + tid;
     const uint4 a = wv[0];
     const uint32_t words[4] = {a.x, a.y, a.z, a.w};
+    // packed per-thread counts: nonzero words << 20 | set bits (block totals fit:
+    // at most 2048 words and 65536 bits)
     unsigned mine = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) mine += __popc(words[q]);
-    // block-wide exclusive scan of `mine`
+    for (int q = 0; q < 4; ++q) mine += (words[q] ? (1u << 20) : 0u) + __popc(words[q]);
     unsigned incl = mine;
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
@@ -121,33 +125,40 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_emit(const __grid_constan
     __syncthreads();
     unsigned warp_off = 0;
     for (int q = 0; q < wid; ++q) warp_off += s_w[q];
-    unsigned off = warp_off + (incl - mine);
+    unsigned off = warp_off + (incl - mine);                 // packed exclusive prefix
+    unsigned total = 0;
+    for (int q = 0; q < kScanThreads / 32; ++q) total += s_w[q];
+    unsigned slot = off >> 20, bits = off & 0xFFFFFu;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        s_word[4 * tid + q] = words[q];
-        s_off[4 * tid + q] = off;
-        off += __popc(words[q]);
+        if (words[q]) {
+            s_word[slot] = words[q];
+            s_off[slot] = bits;
+            s_idx[slot] = (uint16_t)(4 * tid + q);
+            ++slot;
+            bits += __popc(words[q]);
+        }
     }
     if (a.x | a.y | a.z | a.w) wv[0] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     const int64_t base = (int64_t)s_base;
+    const int nnz = (int)(total >> 20);
     const unsigned below = (1u << lane) - 1u;
-    constexpr int kWordsPerWarp = kScanWordsPerBlock / (kScanThreads / 32);
     constexpr int kEmitBatch = 16;
-    static_assert(kWordsPerWarp % kEmitBatch == 0, "emit batches");
-    for (int q = wid * kWordsPerWarp; q < (wid + 1) * kWordsPerWarp; q += kEmitBatch) {
+    constexpr int kWarps = kScanThreads / 32;
+    for (int k0 = wid * kEmitBatch; k0 < nnz; k0 += kWarps * kEmitBatch) {
         uint32_t wd[kEmitBatch], cnt[kEmitBatch];
 #pragma unroll
         for (int u = 0; u < kEmitBatch; ++u) {
-            wd[u] = s_word[q + u];
+            wd[u] = k0 + u < nnz ? s_word[k0 + u] : 0u;
             cnt[u] = 0;
-            if ((wd[u] >> lane) & 1u) cnt[u] = hist[((w0 + q + u) << 5) | lane];
+            if ((wd[u] >> lane) & 1u) cnt[u] = hist[((w0 + s_idx[k0 + u]) << 5) | lane];
         }
 #pragma unroll
         for (int u = 0; u < kEmitBatch; ++u) {
             if ((wd[u] >> lane) & 1u) {
-                const uint32_t key = (uint32_t)((w0 + q + u) << 5) | (uint32_t)lane;
-                const int64_t pos = base + s_off[q + u] + __popc(wd[u] & below);
+                const uint32_t key = (uint32_t)((w0 + s_idx[k0 + u]) << 5) | (uint32_t)lane;
+                const int64_t pos = base + s_off[k0 + u] + __popc(wd[u] & below);
                 hist[key] = 0;
                 if (pos < capacity) {
                     colors[pos] = key;
@@ -156,11 +167,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_emit(const __grid_constan
             }
         }
     }
-    if (b == kScanBlocks - 1 && tid == kScanThreads - 1) {
-        const int64_t total = base + off;   // the last thread of the last block ends at N'
-        *R.n_out[item] = total;
-        if (R.n_user[item]) *R.n_user[item] = total;
-        if (total > capacity) atomicOr(R.status, ST_CAPACITY);
+    if (b == kScanBlocks - 1 && tid == 0) {
+        const int64_t all = base + (total & 0xFFFFFu);      // N': the last block ends at it
+        *R.n_out[item] = all;
+        if (R.n_user[item]) *R.n_user[item] = all;
+        if (all > capacity) atomicOr(R.status, ST_CAPACITY);
     }
 }
 
