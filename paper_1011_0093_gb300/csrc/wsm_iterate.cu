@@ -90,6 +90,8 @@ struct BatchParams {
     ItemDesc item[kMaxBatch];
 };
 
+constexpr int64_t kGroupFloor = 16;   // blocks an image's group gets before the split
+
 // Blocks of one image's group: enough for every lane to hold a color and for
 // every warp to hold a table row.
 __host__ __device__ inline int64_t group_want(int64_t n, int K, int threads) {
@@ -100,10 +102,10 @@ __host__ __device__ inline int64_t group_want(int64_t n, int K, int threads) {
     return w > 1 ? w : 1;
 }
 
-// Split `grid` blocks into one group per image, in proportion to each image's
-// want beyond its first block (every image gets at least one; grid >= n_items),
-// integer arithmetic only so that host and device derive the same split.
-// Returns the number of blocks used.
+// Split `grid` blocks into one group per image: min(want, floor) each, the
+// rest in proportion to each image's want beyond that (every image gets at
+// least one; grid >= n_items), integer arithmetic only so that host and
+// device derive the same split.  Returns the number of blocks used.
 __host__ __device__ inline int split_groups(const int64_t* want, int n_items, int grid,
                                             int* first_blk) {
     int64_t total = 0;
@@ -113,10 +115,17 @@ __host__ __device__ inline int split_groups(const int64_t* want, int n_items, in
         for (int i = 0; i < n_items; ++i) first_blk[i + 1] = first_blk[i] + (int)want[i];
         return first_blk[n_items];
     }
-    const int64_t left = grid - n_items, excess = total - n_items;
+    // every image first gets min(want, floor) blocks: a small image's group
+    // still has the warps for its row build and for the tail of its visits
+    const int64_t floor = (int64_t)grid / n_items < kGroupFloor ? (int64_t)grid / n_items
+                                                                : kGroupFloor;
+    int64_t fixed = 0;
+    for (int i = 0; i < n_items; ++i) fixed += want[i] < floor ? want[i] : floor;
+    const int64_t left = grid - fixed, excess = total - fixed;
     int used = 0;
     for (int i = 0; i < n_items; ++i) {
-        first_blk[i + 1] = 1 + (int)(left * (want[i] - 1) / excess);   // g_i, for now
+        const int64_t f = want[i] < floor ? want[i] : floor;
+        first_blk[i + 1] = (int)(f + left * (want[i] - f) / excess);   // g_i, for now
         used += first_blk[i + 1];
     }
     for (int i = 0; i < n_items && used < grid; ++i)   // the rounding remainder, in order
