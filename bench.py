@@ -23,6 +23,9 @@ replay of a captured CUDA graph (launch shape from the autotuner), against
 ``--form serve`` drives the native serving loop instead: Poisson arrivals of
 requests drawn from 48 seeded images with sides log-uniform in [128, 4096]
 and K in {16, 64, 256}; p50/p99 latency and images/s over 10k requests.
+``--form stability`` reports the stability statistic of Table 4,
+100 (1 - sigma / mu) of the MSE over 100 seeds, for WSM and WSM-C on the 8
+sweep images at K in {32, 64, 128, 256}.
 ``--form grad`` times the differentiable form instead: forward + backward of
 the weighted distortion D(C, X) of a 512x512 image's pixels at K = 64, and
 200 Adam steps of palette refinement from the WSM palette.
@@ -386,6 +389,37 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def adam_graph(wsm, X, C0, assign, h, lr=0.1):
+    """A palette-refinement step (weighted distortion forward, backward, Adam
+    with capturable state) captured into a CUDA graph; returns the palette
+    parameter (reset to C0, optimizer state fresh), the graph and the
+    assignment it warm-starts from."""
+    import torch
+    Cg = C0.clone().requires_grad_(True)
+    opt = torch.optim.Adam([Cg], lr=lr, capturable=True)
+    assign_g = assign.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            opt.zero_grad(set_to_none=True)
+            wsm.weighted_distortion(X, Cg, assign=assign_g, warm_start=True, handle=h).backward()
+            opt.step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    opt.zero_grad(set_to_none=True)
+    with torch.cuda.graph(graph):
+        wsm.weighted_distortion(X, Cg, assign=assign_g, warm_start=True, handle=h).backward()
+        opt.step()
+    with torch.no_grad():                       # start again from C0, fresh moments
+        Cg.copy_(C0)
+        for state in opt.state.values():
+            for v in state.values():
+                if torch.is_tensor(v):
+                    v.zero_()
+    return Cg, graph, assign_g
+
+
 def run_grad(args):
     """Differentiable distortion, forward + backward (dD/dC and dD/dX) per step."""
     import torch
@@ -490,6 +524,17 @@ def run_grad(args):
     adam_ms = (time.perf_counter() - t0) * 1e3
     d_end = float(wsm.weighted_distortion(X, Cp.detach(), assign=assign, warm_start=True,
                                           handle=h))
+    # the same 200 steps, each one replay of a captured CUDA graph (forward,
+    # backward and a capturable Adam step)
+    Cg, graph, assign_g = adam_graph(wsm, X, C0, assign, h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(200):
+        graph.replay()
+    torch.cuda.synchronize()
+    adam_graph_ms = (time.perf_counter() - t0) * 1e3
+    d_end_graph = float(wsm.weighted_distortion(X, Cg.detach(), assign=assign_g, warm_start=True,
+                                                handle=h))
     clk = clocks.stop()
     wsm.wsm_sync_status(h)
 
@@ -529,7 +574,8 @@ def run_grad(args):
         "roofline": {"bound": "hbm", "kernel": "k_grad_bwd", "achieved": bwd_gbs, "peak": hbm,
                      "unit": "GB/s", "frac": bwd_gbs / hbm, "traffic": None,
                      "peak_kind": pk_kind, "bytes_per_launch": bwd_bytes},
-        "adam": {"steps": 200, "lr": 0.1, "ms": adam_ms, "D_start": d_start, "D_end": d_end},
+        "adam": {"steps": 200, "lr": 0.1, "ms": adam_ms, "D_start": d_start, "D_end": d_end,
+                 "graph_ms": adam_graph_ms, "graph_D_end": d_end_graph},
         "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": 4 * args.steps,
     }
@@ -785,13 +831,60 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_stability(args):
+    """Table 4's statistic on the synthetic sweep: 100 seeded runs per image,
+    palette size and variant, all runs of one (image, K, variant) in one batch."""
+    import torch
+
+    import paper_1011_0093_gb300 as wsm
+
+    torch.cuda.set_device(0)
+    images = workload(0)
+    runs = args.runs
+    h = wsm.Handle(K_PALETTE, H * W, H * W)
+    wsm.wsm_reserve_batch(h, runs)
+    table = []
+    t0 = time.perf_counter()
+    for s_img, img in enumerate(images):
+        d = torch.from_numpy(img).cuda()
+        for K in (32, 64, 128, 256):
+            for name, max_iter, eps in (("WSM", 10, 0.0), ("WSM-C", 100, 1e-4)):
+                plan = wsm.BatchPlan([img.shape] * runs, K, [7919 * r + 1 for r in range(runs)],
+                                     max_iter=max_iter, eps=eps, handle=h)
+                plan.load([d] * runs)
+                plan.run()
+                plan.sync()
+                mse = plan.mse.cpu().numpy()
+                iters = plan.iters.cpu().numpy()
+                mu, sigma = float(mse.mean()), float(mse.std())
+                table.append({"image": f"sweep {s_img} (noise {synth.SWEEP_NOISE[s_img]})",
+                              "K": K, "variant": name, "mse_mean": mu, "mse_std": sigma,
+                              "stability": 100.0 * (1.0 - sigma / mu),
+                              "iterations_mean": float(iters.mean())})
+    secs = time.perf_counter() - t0
+    means = {v: float(np.mean([r["stability"] for r in table if r["variant"] == v]))
+             for v in ("WSM", "WSM-C")}
+    line = {"metric": "stability 100(1 - sigma/mu) of the MSE over seeded runs (Table 4)",
+            "form": "stability", "value": means["WSM-C"], "unit": "percent", "n_gpus": 1,
+            "steps": len(table), "warmup": 0, "ms_per_step": 1e3 * secs / len(table),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"8 sweep images 512x512, K in (32, 64, 128, 256), {runs} "
+                                   "seeds each, WSM (10 iterations) and WSM-C (1e-4, <= 100)"},
+            "mean_stability": means, "table": table}
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wsm", choices=["wsm", "reference"])
-    ap.add_argument("--form", default="plain", choices=["plain", "grad", "batch", "serve"])
+    ap.add_argument("--form", default="plain",
+                    choices=["plain", "grad", "batch", "serve", "stability"])
+    ap.add_argument("--runs", type=int, default=100)
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--lanes", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -807,6 +900,8 @@ def main():
         run_batch(args)
     elif args.form == "serve":
         run_serve(args)
+    elif args.form == "stability":
+        run_stability(args)
     else:
         run_gpu(args)
 

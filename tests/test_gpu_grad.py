@@ -193,6 +193,33 @@ def test_adam_refines_the_wsm_palette(wsm, problem):
     assert D_end < 0.99 * D0                # 10 WSM iterations leave room to improve
 
 
+def test_graph_captured_adam_matches_the_eager_loop(wsm, problem):
+    """The refinement step captured into a CUDA graph (forward, backward, a
+    capturable Adam step) and replayed 50 times ends where 50 eager steps end."""
+    import bench
+    _, X, C = problem
+    n = X.shape[0]
+    h = wsm.Handle(K, 1, 1)
+    assign = torch.empty(n, dtype=torch.uint8, device="cuda")
+    wsm.weighted_distortion(X, C, assign=assign, handle=h)
+    Cp = C.clone().requires_grad_(True)
+    opt = torch.optim.Adam([Cp], lr=0.1)
+    a_eager = assign.clone()
+    for _ in range(50):
+        opt.zero_grad()
+        wsm.weighted_distortion(X, Cp, assign=a_eager, warm_start=True, handle=h).backward()
+        opt.step()
+    Cg, graph, a_graph = bench.adam_graph(wsm, X, C, assign, h)
+    for _ in range(50):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert float((Cg.detach() - Cp.detach()).abs().max()) <= 1e-3
+    d_eager = float(wsm.weighted_distortion(X, Cp.detach(), handle=h))
+    d_graph = float(wsm.weighted_distortion(X, Cg.detach(), handle=h))
+    assert abs(d_graph - d_eager) <= 1e-5 * d_eager
+    h.close()
+
+
 def test_empty_input_and_errors(wsm):
     C = torch.rand(8, 3, device="cuda") * 255
     X = torch.empty(0, 3, device="cuda")
