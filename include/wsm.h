@@ -166,8 +166,8 @@ WSM_API int wsm_iterate_stats(wsm_handle* h, int K, int64_t* evaluated, int64_t*
 /* One image of a batch call; fields as for the single-image calls.  Which
  * fields each batch call reads (r) or writes (w):
  *   wsm_reduce_batch      d_rgb n_pixels pixel_stride (r); d_colors d_counts
- *                         (w, device memory of n_pixels entries each, written
- *                         through the const pointers); n_unique (w, host)
+ *                         (w, device memory of n_pixels entries each);
+ *                         n_unique (w, host)
  *   wsm_init_batch        K d_colors n_unique (r); d_centers d_labels (w)
  *   wsm_iterate_batch     K d_colors d_counts n_unique (r); d_centers d_labels (rw)
  *   wsm_map_batch         every field but d_counts (r); d_labels d_index (w)
@@ -177,8 +177,8 @@ typedef struct {
     int64_t n_pixels;
     int pixel_stride;           /* 3 or 4 */
     int K;                      /* 1 <= K <= max_K */
-    const uint32_t* d_colors;   /* [n_unique] ascending */
-    const uint32_t* d_counts;   /* [n_unique] */
+    uint32_t* d_colors;         /* [n_unique] ascending (written by wsm_reduce_batch) */
+    uint32_t* d_counts;         /* [n_unique] (written by wsm_reduce_batch) */
     int64_t n_unique;
     float* d_centers;           /* [K][4], 16-byte aligned */
     uint8_t* d_labels;          /* [n_unique] */

@@ -212,8 +212,8 @@ int reduce_items(wsm_handle* h, const wsm_item* items, int n_items, cudaStream_t
             R.rgb[q] = it.d_rgb;
             R.n[q] = it.n_pixels;
             R.stride[q] = it.pixel_stride;
-            R.colors[q] = const_cast<uint32_t*>(it.d_colors);
-            R.counts[q] = const_cast<uint32_t*>(it.d_counts);
+            R.colors[q] = it.d_colors;
+            R.counts[q] = it.d_counts;
             R.capacity[q] = it.n_pixels;
             R.n_out[q] = h->batch_nu + i0 + q;
             R.n_user[q] = nullptr;

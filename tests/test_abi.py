@@ -50,6 +50,30 @@ def test_argument_errors_without_device(libwsm):
     assert libwsm.wsm_reduce(None, None, 0, 3, None, None, 0, None, None, None) == -1
     assert libwsm.wsm_iterate(None, None, None, 1, 1, None, None, 1, 0.0, None, None,
                               None) == -1
+    # the batch, pipeline, tuning, gradient and serving entry points check first, too
+    assert libwsm.wsm_reduce_batch(None, None, 0, None) == -1
+    assert libwsm.wsm_quantize_batch(None, None, 0, None, 10, 0.0, None, None, None, None) == -1
+    assert libwsm.wsm_quantize_batch_stages(None, None, 0, None, 10, 0.0, None, None, None, 31,
+                                            None) == -1
+    assert libwsm.wsm_autotune_batch(None, None, 0, None, 10, 0.0, 1, None, None) == -1
+    assert libwsm.wsm_set_grid_limit(None, 0) == -1
+    assert libwsm.wsm_set_first_pass_start(None, 1) == -1
+    assert libwsm.wsm_distortion_fwd(None, None, 3, None, 0, None, 3, 4, None, 0, None, None,
+                                     None) == -1
+    assert libwsm.wsm_iterate_noalloc(None, None, 1, 0, None, None, 1, 0.0, None, None,
+                                      None) == -1
+    assert b"K must be in" in libwsm.wsm_last_error()
+    from paper_1011_0093_gb300 import _native
+    srv = C.c_void_p()
+    bad = _native.ServerConfig(16, 1 << 20, 0, 8, 1 << 30)           # no lanes
+    assert libwsm.wsm_server_create(C.byref(srv), C.byref(bad)) == -1
+    assert b"lanes" in libwsm.wsm_last_error()
+    assert srv.value is None
+    assert libwsm.wsm_server_create(None, C.byref(bad)) == -1
+    rid = C.c_uint64(0)
+    assert libwsm.wsm_server_submit(None, None, C.byref(rid)) == -1
+    assert libwsm.wsm_server_wait(None, 1, 0.0, None) == -1
+    assert libwsm.wsm_server_destroy(None) == 0
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
