@@ -413,7 +413,8 @@ extern "C" int wsm_destroy(wsm_handle* h) {
 extern "C" int wsm_reserve_batch(wsm_handle* h, int max_items) {
     int rc = check_handle(h);
     if (rc != WSM_OK) return rc;
-    if (max_items < 1 || max_items > 4096) return fail(WSM_E_INVAL, "max_items must be in [1, 4096]");
+    if (max_items < 1 || max_items > 4096)
+        return fail(WSM_E_INVAL, "max_items must be in [1, 4096]");
     if (max_items <= h->slots) return WSM_OK;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "device sync");
@@ -457,7 +458,8 @@ extern "C" int wsm_init_batch(wsm_handle* h, const wsm_item* items, int n_items,
                               const uint64_t* seeds, wsm_stream stream) {
     int rc = check_handle(h);
     if (rc != WSM_OK) return rc;
-    if (n_items < 0 || (n_items > 0 && (!items || !seeds))) return fail(WSM_E_INVAL, "bad item list");
+    if (n_items < 0 || (n_items > 0 && (!items || !seeds)))
+        return fail(WSM_E_INVAL, "bad item list");
     if (n_items > h->slots)
         return fail(WSM_E_INVAL, "more items than reserved slots (wsm_reserve_batch)");
     for (int i = 0; i < n_items; ++i) {
@@ -467,7 +469,8 @@ extern "C" int wsm_init_batch(wsm_handle* h, const wsm_item* items, int n_items,
             return fail(WSM_E_INVAL, "n_unique must be in [K, max_unique]");
         if (!it.d_colors || !it.d_centers || !it.d_labels)
             return fail(WSM_E_INVAL, "null device pointer");
-        if ((uintptr_t)it.d_centers & 15) return fail(WSM_E_INVAL, "centers must be 16-byte aligned");
+        if ((uintptr_t)it.d_centers & 15)
+            return fail(WSM_E_INVAL, "centers must be 16-byte aligned");
     }
     if (n_items == 0) return WSM_OK;
     cudaStream_t s = (cudaStream_t)stream;

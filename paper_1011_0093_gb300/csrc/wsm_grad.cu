@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_fwd(const __grid_constant
             int mpos = 0;
             for (int j = 1; j < K; ++j) {
                 const float4 e = row[j];
-                if (e.x >= prev) break;              // d[p][t] / 4 >= prev: no closer center further on
+                if (e.x >= prev) break;              // d[p][t] / 4 >= prev: none nearer further on
                 const float d = sq3(x, y, z, e.y, e.z, e.w);
                 if (d <= mn) {                       // the later of equal distances wins
                     mn = d;
