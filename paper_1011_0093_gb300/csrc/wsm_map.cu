@@ -131,7 +131,8 @@ struct MseItems {
 };
 
 // Per-block fixed-point sums as in k_mse_partial, for the image owning the block.
-__global__ void __launch_bounds__(kMseThreads) k_mse_partial_batch(const __grid_constant__ MseItems B) {
+__global__ void __launch_bounds__(kMseThreads)
+    k_mse_partial_batch(const __grid_constant__ MseItems B) {
     __shared__ float4 s_c[WSM_MAX_K];
     __shared__ unsigned long long s_red[kMseThreads / 32];
     const int i = item_of_block(B.first_blk, B.n_items, blockIdx.x);
@@ -207,7 +208,8 @@ int map_items(wsm_handle* h, const wsm_item* items, int n_items, const int64_t* 
             B.slot[q] = i0 + q;
             B.K[q] = it.K;
             const int64_t want = (it.n_pixels + 255) / 256;
-            const int64_t share = std::max<int64_t>(1, budget * it.n_pixels / std::max<int64_t>(total, 1));
+            const int64_t share =
+                std::max<int64_t>(1, budget * it.n_pixels / std::max<int64_t>(total, 1));
             B.first_blk[q + 1] = B.first_blk[q] + (int)std::min(want, share);
         }
         k_gather_batch<<<B.first_blk[m], 256, 0, s>>>(B);
@@ -265,7 +267,8 @@ extern "C" int wsm_map(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, in
                        uint8_t* d_labels, uint8_t* d_index, wsm_stream stream) {
     int rc = check_handle(h);
     if (rc != WSM_OK) return rc;
-    if (pixel_stride != 3 && pixel_stride != 4) return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
+    if (pixel_stride != 3 && pixel_stride != 4)
+        return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
     if (n_pixels < 1 || n_pixels > h->max_pixels)
         return fail(WSM_E_INVAL, "n_pixels must be in [1, max_pixels]");
     if (n_unique < 1 || n_unique > h->max_unique || n_unique > n_pixels)
@@ -308,7 +311,8 @@ extern "C" int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pix
                               wsm_stream stream) {
     int rc = check_handle(h);
     if (rc != WSM_OK) return rc;
-    if (pixel_stride != 3 && pixel_stride != 4) return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
+    if (pixel_stride != 3 && pixel_stride != 4)
+        return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
     if (n_pixels < 0 || n_pixels > h->max_pixels)
         return fail(WSM_E_INVAL, "n_pixels must be in [0, max_pixels]");
     if (K < 1 || K > WSM_MAX_K) return fail(WSM_E_INVAL, "K out of [1, 256]");
@@ -319,7 +323,8 @@ extern "C" int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pix
         return fail(WSM_E_INVAL, "4-byte pixels must be 4-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     int64_t want = (n_pixels + 4 * kMseThreads - 1) / (4 * kMseThreads);
-    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min(kMseMaxBlocks, 4 * h->sms)));
+    int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>(want, std::min(kMseMaxBlocks, 4 * h->sms)));
     unsigned long long* part = reinterpret_cast<unsigned long long*>(h->mse_part);
     k_mse_partial<<<grid, kMseThreads, 0, s>>>(d_rgb, n_pixels, pixel_stride,
                                                 reinterpret_cast<const float4*>(d_centers), K,
@@ -352,8 +357,10 @@ extern "C" int wsm_distortion_batch(wsm_handle* h, const wsm_item* items, int n_
         if (it.n_pixels < 1 || it.n_pixels > h->max_pixels)
             return fail(WSM_E_INVAL, "n_pixels must be in [1, max_pixels]");
         if (it.K < 1 || it.K > WSM_MAX_K) return fail(WSM_E_INVAL, "K out of [1, 256]");
-        if (!it.d_rgb || !it.d_index || !it.d_centers) return fail(WSM_E_INVAL, "null device pointer");
-        if ((uintptr_t)it.d_centers & 15) return fail(WSM_E_INVAL, "centers must be 16-byte aligned");
+        if (!it.d_rgb || !it.d_index || !it.d_centers)
+            return fail(WSM_E_INVAL, "null device pointer");
+        if ((uintptr_t)it.d_centers & 15)
+            return fail(WSM_E_INVAL, "centers must be 16-byte aligned");
         if (it.pixel_stride == 4 && ((uintptr_t)it.d_rgb & 3))
             return fail(WSM_E_INVAL, "4-byte pixels must be 4-byte aligned");
     }

@@ -21,8 +21,9 @@
 
 namespace wsm {
 
-__global__ void k_outputs(int n_items, const int64_t* __restrict__ nu, const Ctrl* __restrict__ ctrl,
-                          int64_t* __restrict__ d_n_unique, int* __restrict__ d_iters) {
+__global__ void k_outputs(int n_items, const int64_t* __restrict__ nu,
+                          const Ctrl* __restrict__ ctrl, int64_t* __restrict__ d_n_unique,
+                          int* __restrict__ d_iters) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_items; i += gridDim.x * blockDim.x) {
         if (d_n_unique) d_n_unique[i] = nu[i];
         if (d_iters) d_iters[i] = ctrl[i].iters_done;
@@ -33,7 +34,8 @@ static int check_batch(wsm_handle* h, const wsm_item* items, int n_items, const 
                        int max_iter) {
     int rc = check_handle(h);
     if (rc != WSM_OK) return rc;
-    if (n_items < 0 || (n_items > 0 && (!items || !seeds))) return fail(WSM_E_INVAL, "bad item list");
+    if (n_items < 0 || (n_items > 0 && (!items || !seeds)))
+        return fail(WSM_E_INVAL, "bad item list");
     if (n_items > h->slots)
         return fail(WSM_E_INVAL, "more items than reserved slots (wsm_reserve_batch)");
     if (max_iter < 0 || max_iter > kMaxTrace)
@@ -45,7 +47,8 @@ static int check_batch(wsm_handle* h, const wsm_item* items, int n_items, const 
         if (it.K < 1 || it.K > h->max_K) return fail(WSM_E_INVAL, "K out of [1, max_K]");
         if (!it.d_colors || !it.d_counts || !it.d_centers || !it.d_labels || !it.d_index)
             return fail(WSM_E_INVAL, "null device pointer");
-        if ((uintptr_t)it.d_centers & 15) return fail(WSM_E_INVAL, "centers must be 16-byte aligned");
+        if ((uintptr_t)it.d_centers & 15)
+            return fail(WSM_E_INVAL, "centers must be 16-byte aligned");
     }
     return WSM_OK;
 }

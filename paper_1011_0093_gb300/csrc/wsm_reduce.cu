@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(256) k_hist24(const __grid_constant__ ReduceIt
 }
 
 // Pass 1 of the compaction: the number of set bits in each block's 2048 words.
-__global__ void __launch_bounds__(kScanThreads) k_scan_count(const __grid_constant__ ReduceItems R) {
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_count(const __grid_constant__ ReduceItems R) {
     const int i = blockIdx.x / kScanBlocks, b = blockIdx.x % kScanBlocks;
     const uint32_t* bitmap = R.bitmap + (size_t)i * kMapWords;
     const uint4 a = reinterpret_cast<const uint4*>(bitmap)[
@@ -245,7 +246,8 @@ extern "C" int wsm_reduce(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels,
                           int64_t* d_n_unique, int64_t* n_unique, wsm_stream stream) {
     int rc = check_handle(h);
     if (rc != WSM_OK) return rc;
-    if (pixel_stride != 3 && pixel_stride != 4) return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
+    if (pixel_stride != 3 && pixel_stride != 4)
+        return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
     if (n_pixels < 0 || n_pixels > h->max_pixels)
         return fail(WSM_E_INVAL, "n_pixels must be in [0, max_pixels]");
     if (capacity < 0) return fail(WSM_E_INVAL, "negative capacity");
@@ -287,7 +289,8 @@ extern "C" int wsm_reduce_batch(wsm_handle* h, wsm_item* items, int n_items, wsm
     for (int i = 0; i < n_items; ++i) {
         rc = check_pixels(h, items[i]);
         if (rc != WSM_OK) return rc;
-        if (!items[i].d_colors || !items[i].d_counts) return fail(WSM_E_INVAL, "null device pointer");
+        if (!items[i].d_colors || !items[i].d_counts)
+            return fail(WSM_E_INVAL, "null device pointer");
     }
     cudaStream_t s = (cudaStream_t)stream;
     rc = reduce_items(h, items, n_items, s);

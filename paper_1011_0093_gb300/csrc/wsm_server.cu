@@ -327,7 +327,8 @@ using namespace wsm;
 extern "C" int wsm_server_create(wsm_server** out, const wsm_server_config* cfg) {
     if (!out || !cfg) return fail(WSM_E_INVAL, "null argument");
     *out = nullptr;
-    if (cfg->max_K < 1 || cfg->max_K > WSM_MAX_K) return fail(WSM_E_INVAL, "max_K must be in [1, 256]");
+    if (cfg->max_K < 1 || cfg->max_K > WSM_MAX_K)
+        return fail(WSM_E_INVAL, "max_K must be in [1, 256]");
     if (cfg->max_pixels < 1 || cfg->max_pixels > WSM_MAX_PIXELS)
         return fail(WSM_E_INVAL, "max_pixels must be in [1, 2^24]");
     if (cfg->lanes < 1 || cfg->lanes > 8) return fail(WSM_E_INVAL, "lanes must be in [1, 8]");

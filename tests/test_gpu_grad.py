@@ -104,7 +104,7 @@ def test_gradient_matches_fp64_central_differences(wsm, problem):
             Dp, _, _, ap = oracle.distortion_grad(Xd, wd, Cp)
             Dm, _, _, am = oracle.distortion_grad(Xd, wd, Cm)
             if not (np.array_equal(ap, a) and np.array_equal(am, a)):
-                continue                                   # a tie is crossed: not differentiable here
+                continue                     # a tie is crossed: not differentiable here
             fd = (Dp - Dm) / (2 * h)
             assert abs(float(gC[k, c]) - fd) <= 1e-5 + 1e-4 * abs(fd), (k, c)
             checked += 1

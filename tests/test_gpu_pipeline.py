@@ -66,7 +66,8 @@ def check_against_single(wsm, plan, imgs, Ks, seeds, max_iter, eps):
             ref = single(wsm, h, img, K, s, max_iter, eps)
             got = plan.result(q)
             assert got["n_unique"] == ref["n_unique"], q
-            assert torch.equal(got["colors"], ref["colors"]) and torch.equal(got["counts"], ref["counts"])
+            assert torch.equal(got["colors"], ref["colors"])
+            assert torch.equal(got["counts"], ref["counts"])
             assert got["iters"] == ref["iters"], q
             assert torch.equal(got["centers"], ref["centers"]), q
             assert torch.equal(got["labels"], ref["labels"]), q
@@ -153,7 +154,8 @@ def test_more_than_one_launch_of_each_kernel(wsm):
     """50 images: four reduction launches (16 per launch) and two persistent
     launches (48 per launch) per step."""
     imgs = [synth.image(40 + (q % 6) * 8, 48 + (q % 4) * 8, 6000 + q, q % 13) for q in range(50)]
-    Ks = [min(4 + (q % 3) * 6, len(np.unique(i.reshape(-1, 3), axis=0))) for q, i in enumerate(imgs)]
+    Ks = [min(4 + (q % 3) * 6, len(np.unique(i.reshape(-1, 3), axis=0)))
+          for q, i in enumerate(imgs)]
     seeds = [q * 31 for q in range(50)]
     plan = wsm.BatchPlan([i.shape for i in imgs], Ks, seeds, max_iter=8)
     plan.load([torch.from_numpy(i) for i in imgs])
@@ -204,5 +206,6 @@ def test_stages_in_separate_calls_and_graphs_equal_one_call(wsm):
     for q in range(len(imgs)):
         a, b, c = whole.result(q), split.result(q), graphs.result(q)
         for r in (b, c):
-            assert r["n_unique"] == a["n_unique"] and r["iters"] == a["iters"] and r["mse"] == a["mse"]
+            assert r["n_unique"] == a["n_unique"] and r["iters"] == a["iters"]
+            assert r["mse"] == a["mse"]
             assert torch.equal(r["centers"], a["centers"]) and torch.equal(r["index"], a["index"])
