@@ -98,7 +98,7 @@ struct wsm_handle {
     int64_t* batch_nu = nullptr;     // [slots] N' of each image of the last wsm_reduce_batch
     double* batch_mse = nullptr;     // [slots] MSE of each image of the last wsm_distortion_batch
     uint32_t* pick = nullptr;        // [slots][max_K] initial center indices (wsm_init_batch)
-    int* plan = nullptr;             // [slots / kMaxBatch + 1][kMaxBatch + 1] device-side block splits
+    int* plan = nullptr;             // [slots / kMaxBatch + 1][kMaxBatch + 1] block splits
     int64_t* host_nu = nullptr;      // pinned mirrors of the three arrays above
     double* host_mse = nullptr;
     uint32_t* host_pick = nullptr;
@@ -264,7 +264,8 @@ __device__ __forceinline__ void build_rows(int K, int G, int b, const float4* s_
             const unsigned lo = (unsigned)kj;
             const int c = lo ? (int)lo - 1 : p;
             const float4 ct = s_c[c];
-            row[rank] = make_float4(__uint_as_float((unsigned)(kj >> 32)) * 0.25f, ct.x, ct.y, ct.z);
+            const float d4 = __uint_as_float((unsigned)(kj >> 32)) * 0.25f;
+            row[rank] = make_float4(d4, ct.x, ct.y, ct.z);
             row_nb[rank] = (uint8_t)c;
         }
         if (lane < 4 && L + lane < K)

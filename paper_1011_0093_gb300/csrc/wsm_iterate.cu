@@ -305,7 +305,8 @@ template <bool kMap, bool kCand>
 __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K, int G, int b,
                                             int WPB, int lane, int wid, unsigned* ticket,
                                             const float4* s_c, unsigned* s_acc, const float4* tab,
-                                            const uint8_t* tab_nb, const uint8_t* grid, uint8_t* lut,
+                                            const uint8_t* tab_nb, const uint8_t* grid,
+                                            uint8_t* lut,
                                             unsigned long long& sse_fx, unsigned long long& ev,
                                             unsigned long long& npix, unsigned long long& nonzero,
                                             bool& bad) {
@@ -439,7 +440,8 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
 }
 
 template <bool kMap, int kThreads>
-__global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sortmeans(const __grid_constant__ BatchParams P) {
+__global__ void __launch_bounds__(kThreads, 1024 / kThreads)
+    k_sortmeans(const __grid_constant__ BatchParams P) {
     // ---- this block's image and group
     const int* first_blk = P.first_dev ? P.first_dev : P.first_blk;
     if ((int)blockIdx.x >= first_blk[P.n_items]) return;   // not needed by any image
@@ -532,7 +534,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sortmeans(const _
                     const int q = grid[grid_cell(col)];
                     if (q != p) {
                         const float4 cq = s_c[q];
-                        atomicMax(s_acc + 4 * K + q, __float_as_uint(sq3(x, y, z, cq.x, cq.y, cq.z)));
+                        const float dq = sq3(x, y, z, cq.x, cq.y, cq.z);
+                        atomicMax(s_acc + 4 * K + q, __float_as_uint(dq));
                     }
                 }
             }
@@ -548,7 +551,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sortmeans(const _
         for (int k = tid; k < K; k += T) {
             unsigned m = 0;
 #pragma unroll
-            for (int c = 0; c < kCopies; ++c) m = max(m, sums[(size_t)(kCopies + c) * s5 + 4 * K + k]);
+            for (int c = 0; c < kCopies; ++c)
+                m = max(m, sums[(size_t)(kCopies + c) * s5 + 4 * K + k]);
             s_thr[k] = 4.f * (__uint_as_float(m) * 1.001f + 1e-3f);
         }
         __syncthreads();
@@ -720,7 +724,8 @@ const IterShape kIterShapes[kNumIterShapes] = {{512, 2}, {256, 4}, {1024, 1}, {2
 static void* sortmeans_fn(bool map_mode, int threads) {
     switch (threads) {
         case 256: return map_mode ? (void*)k_sortmeans<true, 256> : (void*)k_sortmeans<false, 256>;
-        case 1024: return map_mode ? (void*)k_sortmeans<true, 1024> : (void*)k_sortmeans<false, 1024>;
+        case 1024:
+            return map_mode ? (void*)k_sortmeans<true, 1024> : (void*)k_sortmeans<false, 1024>;
         default: return map_mode ? (void*)k_sortmeans<true, 512> : (void*)k_sortmeans<false, 512>;
     }
 }
@@ -1119,11 +1124,13 @@ extern "C" int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_c
         e = cudaMemcpyAsync(&host, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "wsm_iterate_noalloc result copy");
-        if (host.status & ST_TIMEOUT) return fail(WSM_E_TIMEOUT, "a device-side grid barrier timed out");
+        if (host.status & ST_TIMEOUT)
+            return fail(WSM_E_TIMEOUT, "a device-side grid barrier timed out");
         if (host.status & ST_BAD_LABEL) return fail(WSM_E_INVAL, "a membership was >= K");
         if (iters_done) *iters_done = host.iters_done;
         if (sse_trace && host.iters_done > 0) {
-            e = cudaMemcpyAsync(sse_trace, trace, sizeof(double) * std::min(host.iters_done, max_iter),
+            e = cudaMemcpyAsync(sse_trace, trace,
+                                sizeof(double) * std::min(host.iters_done, max_iter),
                                 cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return cuda_fail(e, "wsm_iterate_noalloc trace copy");
