@@ -344,6 +344,14 @@ WSM_API int wsm_quantize_batch_stages(wsm_handle* h, const wsm_item* items, int 
 WSM_API int wsm_batch_stats(wsm_handle* h, int n_items, int64_t* evaluated, int* iters,
                             wsm_stream stream);
 
+/* Self-test of failure detection: two blocks wait at a device barrier that
+ * waits for three, so the wait runs out after limit_ms (1..2000); the
+ * kernel records the timeout in the status word and returns, as the
+ * persistent kernel's barriers do (their limit is 2 s).  Synchronises.
+ * Returns WSM_E_TIMEOUT when the detection works; the handle stays usable.
+ * Errors: WSM_E_INVAL (limit), WSM_E_CUDA. */
+WSM_API int wsm_selftest_barrier_timeout(wsm_handle* h, int limit_ms, wsm_stream stream);
+
 /* Launch shapes of the persistent Sort-Means kernel (no counterpart in the
  * paper: a GPU launch parameter).  Shape s = (threads per block, blocks per
  * SM); the persistent launches of the handle use its current shape.  Every

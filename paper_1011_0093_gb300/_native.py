@@ -89,6 +89,7 @@ SIGNATURES = {
                                    C.POINTER(C.c_int)]),
     "wsm_set_launch_shape": (C.c_int, [_P, C.c_int]),
     "wsm_batch_stats": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "wsm_selftest_barrier_timeout": (C.c_int, [_P, C.c_int, _P]),
     "wsm_set_grid_limit": (C.c_int, [_P, C.c_int]),
     "wsm_set_first_pass_start": (C.c_int, [_P, C.c_int]),
     "wsm_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(ServerConfig)]),

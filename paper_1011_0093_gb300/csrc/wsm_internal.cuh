@@ -162,10 +162,11 @@ __device__ __forceinline__ unsigned add_release(unsigned* p, unsigned v) {
 // image's group of it).  Thread 0 of each block adds 1 to a counter that only
 // grows (release), and waits (acquire) until it reaches the next multiple of
 // nblocks, i.e. until every block has arrived at this barrier.  The wait has
-// a time limit: past it *status gets ST_TIMEOUT and the function returns false
-// in every thread of the block.  Memory written before the barrier by any of
+// a time limit (limit_ns): past it *status gets ST_TIMEOUT and the function
+// returns false in every thread of the block.  Memory written before the barrier by any of
 // the blocks is visible to all of them after it.
-__device__ __forceinline__ bool grid_sync(unsigned* counter, unsigned* status, unsigned nblocks) {
+__device__ __forceinline__ bool grid_sync(unsigned* counter, unsigned* status, unsigned nblocks,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
     __shared__ unsigned s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -175,7 +176,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* counter, unsigned* status, u
         if ((int)(ld_acquire(counter) - target) < 0) {
             unsigned long long t0 = global_ns();
             while ((int)(ld_acquire(counter) - target) < 0) {
-                if (global_ns() - t0 > kWaitLimitNs) {
+                if (global_ns() - t0 > limit_ns) {
                     atomicOr(status, ST_TIMEOUT);
                     ok = 0u;
                     break;

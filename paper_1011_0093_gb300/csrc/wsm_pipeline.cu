@@ -53,9 +53,32 @@ static int check_batch(wsm_handle* h, const wsm_item* items, int n_items, const 
     return WSM_OK;
 }
 
+// Two blocks meet at a barrier that waits for three: the wait can only run
+// out (the failure the persistent kernel's barriers guard against).
+__global__ void k_barrier_timeout(unsigned* counter, unsigned* status,
+                                  unsigned long long limit_ns) {
+    grid_sync(counter, status, gridDim.x + 1, limit_ns);
+}
+
 }  // namespace wsm
 
 using namespace wsm;
+
+extern "C" int wsm_selftest_barrier_timeout(wsm_handle* h, int limit_ms, wsm_stream stream) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (limit_ms < 1 || limit_ms > 2000) return fail(WSM_E_INVAL, "limit_ms must be in [1, 2000]");
+    cudaStream_t s = (cudaStream_t)stream;
+    // slot 0's barrier counter, cleared before and after (the next launch clears it too)
+    cudaError_t e = cudaMemsetAsync(&h->slot_ctrl[0].bar_count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test set-up");
+    k_barrier_timeout<<<2, 32, 0, s>>>(&h->slot_ctrl[0].bar_count, &h->ctrl->status,
+                                       (unsigned long long)limit_ms * 1000000ull);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(&h->slot_ctrl[0].bar_count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
+    return read_status(h, s);
+}
 
 extern "C" int wsm_quantize_batch_stages(wsm_handle* h, const wsm_item* items, int n_items,
                                          const uint64_t* seeds, int max_iter, double eps,

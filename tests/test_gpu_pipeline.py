@@ -209,3 +209,18 @@ def test_stages_in_separate_calls_and_graphs_equal_one_call(wsm):
             assert r["n_unique"] == a["n_unique"] and r["iters"] == a["iters"]
             assert r["mse"] == a["mse"]
             assert torch.equal(r["centers"], a["centers"]) and torch.equal(r["index"], a["index"])
+
+
+def test_a_barrier_that_can_never_complete_times_out_and_the_handle_stays_usable(wsm):
+    """Failure detection without a fault: the device barrier's bounded wait
+    runs out, the status word says so, and the next call works."""
+    from paper_1011_0093_gb300 import _native as N
+    img = synth.image(64, 64, 3, 9)
+    with wsm.Handle(16, 64 * 64) as h:
+        rc = N.lib().wsm_selftest_barrier_timeout(h.ptr, 50, None)
+        assert rc == -4                                          # WSM_E_TIMEOUT
+        assert b"timed out" in N.lib().wsm_last_error()
+        wsm.wsm_sync_status(h)                                   # the report was consumed
+        q = wsm.quantize(torch.from_numpy(img).cuda(), 16, 1, max_iter=5, handle=h)
+        ref = wsm.quantize(torch.from_numpy(img).cuda(), 16, 1, max_iter=5)
+        assert torch.equal(q.centers, ref.centers) and torch.equal(q.index, ref.index)
