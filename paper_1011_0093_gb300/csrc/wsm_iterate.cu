@@ -314,6 +314,8 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
     // chunks G * WPB + t in the order of the tickets t it draws from the
     // slot's counter (each ticket drawn one chunk ahead), so the warps of
     // the group finish together whatever the cost of their colors.
+    // per-lane counts of this pass fit 32 bits (at most 2^24 pixels per image)
+    unsigned ev32 = 0, npix32 = 0, nz32 = 0;
     int64_t cur = ((int64_t)b * WPB + wid) * kChunk;
     int64_t nxt = n;
     {
@@ -377,7 +379,7 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
                     scan_p = false;
                     lab = r.best;
                     mn = r.mn;
-                    ev += (unsigned long long)r.visits;
+                    ev32 += (unsigned)r.visits;
                 }
             }
         }
@@ -415,7 +417,7 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
                 if (e.x >= prev) break;        // d[p][t] >= 4 prev_dist: stop
                 WSM_VISIT(e, j);
             }
-            ev += (unsigned long long)j;       // c_p plus the j - 1 visited centers
+            ev32 += (unsigned)j;               // c_p plus the j - 1 visited centers
             lab = mpos ? tab_nb[(size_t)p * K + mpos] : p;
         }
         if (active) {
@@ -429,14 +431,17 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
                 atomicAdd(s_acc + 4 * lab + 3, cnt);
                 atomicMax(s_acc + 4 * K + lab, __float_as_uint(mn));
                 sse_fx += sse_fixed(cnt, mn);
-                npix += cnt;
-                nonzero += mn > 0.f;
+                npix32 += cnt;
+                nz32 += mn > 0.f;
             }
         }
         const unsigned t = __shfl_sync(0xFFFFFFFFu, t_after, 0);
         cur = nxt;
         nxt = cur < n ? ((int64_t)G * WPB + t) * kChunk : n;
     }
+    ev += ev32;
+    npix += npix32;
+    nonzero += nz32;
 }
 
 template <bool kMap, int kThreads>
