@@ -26,6 +26,9 @@ and K in {16, 64, 256}; p50/p99 latency and images/s over 10k requests.
 ``--form stability`` reports the stability statistic of Table 4,
 100 (1 - sigma / mu) of the MSE over 100 seeds, for WSM and WSM-C on the 8
 sweep images at K in {32, 64, 128, 256}.
+``--form hbm`` times the HBM-bound steps on 4 images of 4096x4096: the
+unique-color reduction (a1), the mapping (a7) and the MSE (a8), each against
+the measured HBM peak.
 ``--form grad`` times the differentiable form instead: forward + backward of
 the weighted distortion D(C, X) of a 512x512 image's pixels at K = 64, and
 200 Adam steps of palette refinement from the WSM palette.
@@ -876,6 +879,67 @@ def run_stability(args):
     h.close()
 
 
+def _hbm_image(q):
+    return synth.image(4096, 4096, 12000 + q, (8 * q + 5) % 25)
+
+
+def run_hbm(args):
+    """The HBM-bound stages on 4096x4096 images, each timed on its own (CUDA
+    events around the stage, inputs resident, L2 flushed before each)."""
+    import multiprocessing as mp
+    n_img = 4
+    with mp.get_context("spawn").Pool(n_img) as pool:
+        images = pool.map(_hbm_image, range(n_img))          # before any CUDA call
+    import torch
+
+    import paper_1011_0093_gb300 as wsm
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    plan = wsm.BatchPlan([im.shape for im in images], K_PALETTE, list(range(n_img)), max_iter=2)
+    plan.load([torch.from_numpy(im) for im in images])
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stages = {"reduce": wsm.STAGE_REDUCE, "init+iterate": wsm.STAGE_INIT | wsm.STAGE_ITERATE,
+              "map": wsm.STAGE_MAP, "mse": wsm.STAGE_DISTORTION}
+    times = {k: [] for k in stages}
+    for rep in range(args.warmup + args.steps):
+        for name, st in stages.items():
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.run(st)
+            b.record(stream)
+            b.synchronize()
+            if rep >= args.warmup:
+                times[name].append(a.elapsed_time(b))
+    plan.sync()
+    n_unique = [int(v) for v in plan.n_unique.cpu()]
+    N = sum(im.shape[0] * im.shape[1] for im in images)
+    NU = sum(n_unique)
+    algo = {"reduce": 3 * N + 8 * NU,                     # pixels in, (color, count) out
+            "map": 3 * N + N + NU,                        # pixels in, index out, table entries
+            "mse": 4 * N}                                 # pixels and index in
+    pk, pk_kind = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    rows = {}
+    for name, nbytes in algo.items():
+        ms = statistics.median(times[name])
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        rows[name] = {"ms": ms, "algorithmic_bytes": nbytes, "GB/s": gbs, "frac": gbs / hbm}
+    line = {"metric": "HBM-bound steps on 4096x4096 images: algorithmic GB/s vs measured HBM peak",
+            "form": "hbm", "value": rows["reduce"]["GB/s"], "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows["reduce"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": f"{n_img} images 4096x4096 (noise 5..), K=256",
+                       "pixels": N, "unique_colors": n_unique,
+                       "l2": "flushed before each stage (256 MiB write)"},
+            "stages": rows, "peak": hbm, "peak_kind": pk_kind}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -883,7 +947,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wsm", choices=["wsm", "reference"])
     ap.add_argument("--form", default="plain",
-                    choices=["plain", "grad", "batch", "serve", "stability"])
+                    choices=["plain", "grad", "batch", "serve", "stability", "hbm"])
     ap.add_argument("--runs", type=int, default=100)
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--lanes", type=int, default=2)
@@ -902,6 +966,8 @@ def main():
         run_serve(args)
     elif args.form == "stability":
         run_stability(args)
+    elif args.form == "hbm":
+        run_hbm(args)
     else:
         run_gpu(args)
 
