@@ -27,8 +27,9 @@ and K in {16, 64, 256}; p50/p99 latency and images/s over 10k requests.
 100 (1 - sigma / mu) of the MSE over 100 seeds, for WSM and WSM-C on the 8
 sweep images at K in {32, 64, 128, 256}.
 ``--form hbm`` times the HBM-bound steps on 4 images of 4096x4096: the
-unique-color reduction (a1), the mapping (a7) and the MSE (a8), each against
-the measured HBM peak.
+unique-color reduction, the pixel mapping and the per-pixel MSE of the
+index images, each against the measured HBM peak (the final assignment and
+the pipeline's MSE from it are timed beside them).
 ``--form grad`` times the differentiable form instead: forward + backward of
 the weighted distortion D(C, X) of a 512x512 image's pixels at K = 64, and
 200 Adam steps of palette refinement from the WSM palette.
@@ -260,11 +261,12 @@ def run_gpu(args):
     wsm.wsm_set_first_pass_start(plan.handle, True)
     plan.run(wsm.STAGE_REDUCE | wsm.STAGE_INIT | wsm.STAGE_ITERATE)
     executed, _ = plan.stats()
-    # one step = three captured graphs replayed back to back: a1-a2, a3-a6
-    # (one persistent launch over the 8 images), a7-a8; events between them
+    # one step = three captured graphs replayed back to back: unique colors +
+    # init, the iterations (one persistent launch over the 8 images), final
+    # assignment + mapping + MSE; events between them
     # time the iterations inside the timed region
     parts = (wsm.STAGE_REDUCE | wsm.STAGE_INIT, wsm.STAGE_ITERATE,
-             wsm.STAGE_MAP | wsm.STAGE_DISTORTION)
+             wsm.STAGE_MAP | wsm.STAGE_INDEX | wsm.STAGE_DISTORTION)
     plan.capture(parts)
     it_events = []
 
@@ -901,7 +903,9 @@ def run_hbm(args):
     plan.load([torch.from_numpy(im) for im in images])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stages = {"reduce": wsm.STAGE_REDUCE, "init+iterate": wsm.STAGE_INIT | wsm.STAGE_ITERATE,
-              "map": wsm.STAGE_MAP, "mse": wsm.STAGE_DISTORTION}
+              "assign": wsm.STAGE_MAP, "index": wsm.STAGE_INDEX,
+              "mse_from_assign": wsm.STAGE_DISTORTION,
+              "mse_pixels": None}                # Eq. 2 over the pixels and the index images
     times = {k: [] for k in stages}
     for rep in range(args.warmup + args.steps):
         for name, st in stages.items():
@@ -909,7 +913,10 @@ def run_hbm(args):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            plan.run(st)
+            if st is None:
+                wsm.wsm_distortion_batch(plan.handle, plan.images, sync=False)
+            else:
+                plan.run(st)
             b.record(stream)
             b.synchronize()
             if rep >= args.warmup:
@@ -919,15 +926,16 @@ def run_hbm(args):
     N = sum(im.shape[0] * im.shape[1] for im in images)
     NU = sum(n_unique)
     algo = {"reduce": 3 * N + 8 * NU,                     # pixels in, (color, count) out
-            "map": 3 * N + N + NU,                        # pixels in, index out, table entries
-            "mse": 4 * N}                                 # pixels and index in
+            "index": 3 * N + N + NU,                      # pixels in, index out, table entries
+            "mse_pixels": 4 * N}                          # pixels and index in
     pk, pk_kind = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
     rows = {}
-    for name, nbytes in algo.items():
-        ms = statistics.median(times[name])
-        gbs = nbytes / (ms * 1e-3) / 1e9
-        rows[name] = {"ms": ms, "algorithmic_bytes": nbytes, "GB/s": gbs, "frac": gbs / hbm}
+    for name in stages:
+        rows[name] = {"ms": statistics.median(times[name])}
+        if name in algo:
+            gbs = algo[name] / (rows[name]["ms"] * 1e-3) / 1e9
+            rows[name].update({"algorithmic_bytes": algo[name], "GB/s": gbs, "frac": gbs / hbm})
     line = {"metric": "HBM-bound steps on 4096x4096 images: algorithmic GB/s vs measured HBM peak",
             "form": "hbm", "value": rows["reduce"]["GB/s"], "unit": "GB/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows["reduce"]["ms"],

@@ -127,8 +127,8 @@ WSM_API int wsm_reduce(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, in
  * membership starts at 0: d_labels[i] = 0.  Asynchronous.
  *   d_colors   [n_unique]; d_centers [K][4] out; d_labels [n_unique] out
  * Errors: WSM_E_INVAL (K < 1, K > max_K, K > n_unique). */
-WSM_API int wsm_init(wsm_handle* h, const uint32_t* d_colors, int64_t n_unique, int K, uint64_t seed,
-             float* d_centers, uint8_t* d_labels, wsm_stream stream);
+WSM_API int wsm_init(wsm_handle* h, const uint32_t* d_colors, int64_t n_unique, int K,
+                     uint64_t seed, float* d_centers, uint8_t* d_labels, wsm_stream stream);
 
 /* Algorithm 2 with the Sec. 3.2 termination rule, in one persistent
  * cooperative launch.  Each iteration: the K x K squared center distances
@@ -318,16 +318,22 @@ enum {
     WSM_STAGE_REDUCE = 1,      /* Sec. 2 unique colors (writes N' on the device) */
     WSM_STAGE_INIT = 2,        /* Algorithm 2 initialisation (needs REDUCE before) */
     WSM_STAGE_ITERATE = 4,     /* Sort-Means iterations, Sec. 3.2 stop rule; d_n_unique, d_iters */
-    WSM_STAGE_MAP = 8,         /* final assignment + pixel mapping */
-    WSM_STAGE_DISTORTION = 16, /* Eq. 2 MSE; d_mse */
-    WSM_STAGE_ALL = 31
+    WSM_STAGE_MAP = 8,         /* final assignment: unique colors' labels, color->label table */
+    WSM_STAGE_INDEX = 32,      /* pixel mapping: the index image (needs MAP before) */
+    WSM_STAGE_DISTORTION = 16, /* Eq. 2 MSE from the final assignment; d_mse (needs MAP) */
+    WSM_STAGE_ALL = 63
 };
 
 /* The stages of wsm_quantize_batch named by the `stages` bits, in the order
- * above, on the device state the earlier stages left (the handle's N'
- * values, the items' buffers).  Running the stages in several calls, e.g. to
- * time them or to capture each into its own CUDA graph, gives exactly the
- * results of one wsm_quantize_batch call.
+ * listed above (INDEX before DISTORTION), on the device state the earlier
+ * stages left (the handle's N' values, the items' buffers, the squared-error
+ * sum of the last final assignment).  Running the stages in several calls,
+ * e.g. to time them or to capture each into its own CUDA graph, gives
+ * exactly the results of one wsm_quantize_batch call.  DISTORTION reads no
+ * pixels: the final assignment (MAP) sums, over the unique colors,
+ * count x squared distance to the assigned center with each pixel's term
+ * truncated to 2^-20 as wsm_distortion truncates it, so the MSE equals
+ * wsm_distortion's on the index image bit for bit.
  * Errors: as wsm_quantize_batch; WSM_E_INVAL for unknown stage bits. */
 WSM_API int wsm_quantize_batch_stages(wsm_handle* h, const wsm_item* items, int n_items,
                                       const uint64_t* seeds, int max_iter, double eps,

@@ -10,8 +10,8 @@ fixed batch's buffers and captures the whole path into a CUDA graph;
 ``distortion`` wraps the weighted distortion and its gradients as a
 torch.autograd.Function.  PyTorch only provides device memory and streams.
 """
-from ._native import (MAX_K, MAX_PIXELS, STAGE_ALL, STAGE_DISTORTION, STAGE_INIT,
-                      STAGE_ITERATE, STAGE_MAP, STAGE_REDUCE, Handle, WsmError, lib,
+from ._native import (MAX_K, MAX_PIXELS, STAGE_ALL, STAGE_DISTORTION, STAGE_INDEX,
+                      STAGE_INIT, STAGE_ITERATE, STAGE_MAP, STAGE_REDUCE, Handle, WsmError, lib,
                       pipeline_items, wsm_autotune_batch, wsm_batch_stats, wsm_distortion,
                       wsm_distortion_batch, wsm_distortion_bwd, wsm_distortion_fwd, wsm_init,
                       wsm_init_batch, wsm_iterate, wsm_iterate_batch, wsm_iterate_noalloc,
@@ -26,7 +26,7 @@ from .quantize import Quantized, quantize, quantize_batch
 
 __all__ = [
     "MAX_K", "MAX_PIXELS", "Handle", "WsmError", "lib",
-    # one image: a1 .. a8
+    # one image, step by step
     "wsm_reduce", "wsm_init", "wsm_iterate", "wsm_iterate_stats", "wsm_iterate_noalloc",
     "wsm_map", "wsm_distortion", "wsm_sync_status", "Quantized", "quantize",
     # batches of images
@@ -34,8 +34,8 @@ __all__ = [
     "wsm_map_batch", "wsm_distortion_batch", "quantize_batch",
     # the whole path with N' on the device, graphs, launch shapes, autotuner
     "wsm_quantize_batch", "pipeline_items", "STAGE_REDUCE", "STAGE_INIT", "STAGE_ITERATE",
-    "STAGE_MAP", "STAGE_DISTORTION", "STAGE_ALL", "wsm_autotune_batch", "wsm_launch_shape",
-    "wsm_set_launch_shape", "wsm_set_grid_limit", "wsm_set_first_pass_start",
+    "STAGE_MAP", "STAGE_INDEX", "STAGE_DISTORTION", "STAGE_ALL", "wsm_autotune_batch",
+    "wsm_launch_shape", "wsm_set_launch_shape", "wsm_set_grid_limit", "wsm_set_first_pass_start",
     "wsm_batch_stats", "BatchPlan",
     # serving
     "Server",

@@ -476,7 +476,8 @@ def _seeds(seeds, n):
 
 
 STAGE_REDUCE, STAGE_INIT, STAGE_ITERATE, STAGE_MAP, STAGE_DISTORTION = 1, 2, 4, 8, 16
-STAGE_ALL = 31
+STAGE_INDEX = 32
+STAGE_ALL = 63
 
 
 def wsm_quantize_batch(h: Handle, items, n_items: int, seeds, max_iter: int, eps: float,

@@ -56,6 +56,8 @@ struct Ctrl {
     unsigned ticket[2];        // chunks handed out in the assignment pass, by pass parity
     int64_t n_unique;          // N' of the last wsm_reduce
     double mse;                // host mirror slot of the last wsm_distortion
+    unsigned long long map_sse;    // sum over colors of count * ||x - c||^2 in units of
+                                   // 2^-20 (each term truncated) of the last final assignment
 };
 
 }  // namespace wsm
@@ -129,11 +131,11 @@ int launch_sortmeans(wsm_handle* h, bool map_mode, const uint32_t* colors, const
                      int64_t n, int K, float* centers, uint8_t* labels, int max_iter, double eps,
                      cudaStream_t s);
 int launch_map_items(wsm_handle* h, const wsm_item* items, int n_items, int slot0,
-                     const int64_t* n_dev, cudaStream_t s);
-int map_items(wsm_handle* h, const wsm_item* items, int n_items, const int64_t* n_dev,
+                     const int64_t* n_dev, bool sse, cudaStream_t s);
+int map_items(wsm_handle* h, const wsm_item* items, int n_items, const int64_t* n_dev, bool sse,
               cudaStream_t s);
-int distortion_items(wsm_handle* h, const wsm_item* items, int n_items, double* d_mse,
-                     const int64_t* n_dev, cudaStream_t s);
+int pixel_items(wsm_handle* h, const wsm_item* items, int n_items, bool gather, double* d_mse,
+                const int64_t* n_dev, cudaStream_t s);
 void free_slots(wsm_handle* h);
 
 // ---------------------------------------------------------------------------
@@ -227,22 +229,50 @@ __device__ __forceinline__ unsigned long long row_key(float d, int t, int p) {
     return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(t == p ? 0 : t + 1);
 }
 
-// The rows p = b, b + G, ... of one image's table, one row per warp at a time.
-// Row p keeps the centers t with d[p][t] < thr[p] (p itself always); the
-// rank of a key among the kept keys (keys are distinct) is its entry
-// position.  Four entries with an infinite bound follow the kept ones.
+// Barrier of the ts warps of team m (ts a power of two; a named barrier
+// 1 + m when ts > 1, so at most 15 teams of several warps per block).
+__device__ __forceinline__ void team_sync(int m, int ts) {
+    if (ts == 1) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(m + 1), "r"(ts * 32) : "memory");
+}
+
+// Warps per row-building team: the largest power of two ts <= WPB that
+// still leaves at least K teams over the image's G blocks (one row each),
+// counting only team sizes that give at most 8 teams per block; 1 (one warp
+// per row, several rows per warp) when even single warps are fewer than K.
+__device__ __forceinline__ int row_team_size(int K, int G, int WPB) {
+    int ts = 1;
+    for (int c = 2; c <= WPB; c *= 2)
+        if (WPB / c <= 8 && (long long)G * (WPB / c) >= K) ts = c;
+    return ts;
+}
+
+// The rows of one image's table, built by teams of ts warps: team m of
+// block b is team number m * G + b of the image and builds rows team,
+// team + (number of teams), ...  Row p keeps the centers t with
+// d[p][t] < thr[p] (p itself always); the rank of a key among the kept keys
+// (keys are distinct, so the order in which they were collected does not
+// matter) is its entry position.  The team's threads split the comparisons
+// of a rank when there are more of them than kept keys.  Four entries with an
+// infinite bound follow the kept ones.
 __device__ __forceinline__ void build_rows(int K, int G, int b, const float4* s_c,
                                            const float* s_thr, unsigned long long* s_wkey,
                                            float4* tab, uint8_t* tab_nb) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, WPB = blockDim.x >> 5;
-    unsigned long long* key = s_wkey + (size_t)wid * K;        // this warp's buffer
+    __shared__ int s_len[32];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, WPB = blockDim.x >> 5;
+    const int ts = row_team_size(K, G, WPB), TT = ts * 32;
+    const int m = wid / ts, r = threadIdx.x - m * TT;          // team, thread in team
+    const int teams = G * (WPB / ts);
+    unsigned long long* key = s_wkey + (size_t)m * ts * K;     // the team's buffer: ts * K
+    int* rank_part = reinterpret_cast<int*>(key + K);           // [K] when ts > 1
     const unsigned below = (1u << lane) - 1u;
-    for (int p = b + wid * G; p < K; p += G * WPB) {
+    for (int p = m * G + b; p < K; p += teams) {
         const float4 cp = s_c[p];
         const float bound = s_thr[p];
-        int L = 0;
-        for (int t0 = 0; t0 < K; t0 += 32) {
-            const int t = t0 + lane;
+        if (r == 0) s_len[m] = 0;
+        team_sync(m, ts);
+        for (int t0 = 0; t0 < K; t0 += TT) {
+            const int t = t0 + r;
             float d = 0.f;
             bool keep = false;
             if (t < K) {
@@ -251,17 +281,39 @@ __device__ __forceinline__ void build_rows(int K, int G, int b, const float4* s_
                 keep = d < bound || t == p;
             }
             const unsigned vote = __ballot_sync(0xFFFFFFFFu, keep);
-            if (keep) key[L + __popc(vote & below)] = row_key(d, t, p);
-            L += __popc(vote);
+            int base = 0;
+            if (lane == 0 && vote) base = atomicAdd(&s_len[m], __popc(vote));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (keep) key[base + __popc(vote & below)] = row_key(d, t, p);
         }
-        __syncwarp();
+        team_sync(m, ts);
+        const int L = s_len[m];
         float4* row = tab + (size_t)p * K;
         uint8_t* row_nb = tab_nb + (size_t)p * K;
-        for (int j = lane; j < L; j += 32) {
+        const int H = ts > 1 ? max(1, TT / L) : 1;               // threads per kept key
+        if (H > 1) {
+            for (int j = r; j < L; j += TT) rank_part[j] = 0;
+            team_sync(m, ts);
+            const int span = (L + H - 1) / H;
+            for (int u = r; u < L * H; u += TT) {
+                const int j = u % L, h = u / L;
+                const unsigned long long kj = key[j];
+                int cnt = 0;
+                const int k1 = min(L, (h + 1) * span);
+                for (int k = h * span; k < k1; ++k) cnt += key[k] < kj;
+                if (cnt) atomicAdd(rank_part + j, cnt);
+            }
+            team_sync(m, ts);
+        }
+        for (int j = r; j < L; j += TT) {
             const unsigned long long kj = key[j];
             int rank = 0;
+            if (H > 1) {
+                rank = rank_part[j];
+            } else {
 #pragma unroll 8
-            for (int k = 0; k < L; ++k) rank += key[k] < kj;
+                for (int k = 0; k < L; ++k) rank += key[k] < kj;
+            }
             const unsigned lo = (unsigned)kj;
             const int c = lo ? (int)lo - 1 : p;
             const float4 ct = s_c[c];
@@ -269,9 +321,9 @@ __device__ __forceinline__ void build_rows(int K, int G, int b, const float4* s_
             row[rank] = make_float4(d4, ct.x, ct.y, ct.z);
             row_nb[rank] = (uint8_t)c;
         }
-        if (lane < 4 && L + lane < K)
-            row[L + lane] = make_float4(__int_as_float(0x7f800000), 0.f, 0.f, 0.f);
-        __syncwarp();
+        if (r < 4 && L + r < K)
+            row[L + r] = make_float4(__int_as_float(0x7f800000), 0.f, 0.f, 0.f);
+        team_sync(m, ts);
     }
 }
 

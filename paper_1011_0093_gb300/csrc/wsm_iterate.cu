@@ -329,7 +329,7 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
     if (cur + lane < n) {
         col_n = __ldg(I.colors + cur + lane);
         lab_n = I.labels[cur + lane];
-        if (!kMap) cnt_n = __ldg(I.counts + cur + lane);
+        if (!kMap || I.counts) cnt_n = __ldg(I.counts + cur + lane);
     }
     while (cur < n) {
         const int64_t i = cur + lane;
@@ -342,7 +342,7 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
             if (nxt + lane < n) {
                 col_n = __ldg(I.colors + nxt + lane);
                 lab_n = I.labels[nxt + lane];
-                if (!kMap) cnt_n = __ldg(I.counts + nxt + lane);
+                if (!kMap || I.counts) cnt_n = __ldg(I.counts + nxt + lane);
             }
             if (lane == 0) t_after = atomicAdd(ticket, 1u);   // used after this chunk
         }
@@ -424,6 +424,9 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
             if (lab != p0) I.labels[i] = (uint8_t)lab;
             if (kMap) {
                 lut[col & 0xFFFFFFu] = (uint8_t)lab;
+                // Eq. 2 over the pixels of this color, each pixel's squared
+                // distance truncated to 2^-20 units as the per-pixel MSE does
+                sse_fx += (unsigned long long)cnt * sse_fixed(1u, mn);
             } else {
                 atomicAdd(s_acc + 4 * lab + 0, cnt * ((col >> 16) & 255u));
                 atomicAdd(s_acc + 4 * lab + 1, cnt * ((col >> 8) & 255u));
@@ -601,6 +604,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
             unsigned long long t = 0;
             for (int w = 0; w < WPB; ++w) t += s_red[tid][w];
             if (kMap) {
+                if (tid == 0 && t) atomicAdd(&ctrl->map_sse, t);
                 if (tid == 1 && t) atomicAdd(&ctrl->evaluated, t);
             } else if (t) {
                 atomicAdd(sums64 + (size_t)(buf * kCopies + copy) * 4 + tid, t);
@@ -849,13 +853,14 @@ int launch_sortmeans(wsm_handle* h, bool map_mode, const uint32_t* colors, const
 }
 
 // The final assignment of n_items images (slots slot0, slot0 + 1, ...) in
-// one persistent launch in map mode.
+// one persistent launch in map mode; with sse, each slot's map_sse also gets
+// the image's squared-error sum (from the items' counts).
 int launch_map_items(wsm_handle* h, const wsm_item* items, int n_items, int slot0,
-                     const int64_t* n_dev, cudaStream_t s) {
+                     const int64_t* n_dev, bool sse, cudaStream_t s) {
     ItemDesc d[kMaxBatch];
     for (int q = 0; q < n_items; ++q) {
         d[q].colors = items[q].d_colors;
-        d[q].counts = nullptr;
+        d[q].counts = sse ? items[q].d_counts : nullptr;
         d[q].labels = items[q].d_labels;
         d[q].centers = reinterpret_cast<float4*>(items[q].d_centers);
         d[q].n = n_dev ? items[q].n_pixels : items[q].n_unique;

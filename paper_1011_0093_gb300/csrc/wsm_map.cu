@@ -8,47 +8,13 @@
 // entries of this image are written, and every pixel's color is one of them.
 #include <algorithm>
 
-#include "wsm_internal.cuh"
+#include "wsm_pixels.cuh"
 
 namespace wsm {
 
 
-__global__ void __launch_bounds__(256) k_gather(const uint8_t* __restrict__ rgb, int64_t n,
-                                                int stride, const uint8_t* __restrict__ lut,
-                                                uint8_t* __restrict__ index) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x)
-        index[p] = lut[pixel_key(rgb, p, stride)];
-}
-
-// The gather of a batch: image i owns blocks [first_blk[i], first_blk[i+1])
-// and reads the color->label table of its slot.
-struct GatherBatch {
-    int n_items;
-    int first_blk[kMaxBatch + 1];
-    const uint8_t* rgb[kMaxBatch];
-    uint8_t* index[kMaxBatch];
-    int64_t n[kMaxBatch];
-    int stride[kMaxBatch];
-    int slot[kMaxBatch];
-    int K[kMaxBatch];
-    const uint8_t* lut;        // slot s at lut + s * 2^24
-    const int64_t* n_dev;      // if set: an image with n_dev[slot] < K was skipped (index 0)
-};
-
-__global__ void __launch_bounds__(256) k_gather_batch(const __grid_constant__ GatherBatch B) {
-    const int i = item_of_block(B.first_blk, B.n_items, blockIdx.x);
-    const int g0 = B.first_blk[i], G = B.first_blk[i + 1] - g0;
-    const uint8_t* lut = B.lut + (size_t)B.slot[i] * kHistBins;
-    const int64_t n = B.n[i];
-    const bool skipped = B.n_dev && B.n_dev[B.slot[i]] < B.K[i];
-    for (int64_t p = (int64_t)(blockIdx.x - g0) * blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)G * blockDim.x)
-        B.index[i][p] = skipped ? 0 : lut[pixel_key(B.rgb[i], p, B.stride[i])];
-}
-
-constexpr int kMseThreads = 256;
-constexpr int kMseMaxBlocks = 1024;
+constexpr int kPixThreads = 256;
+constexpr int kMseMaxBlocks = 1024;   // partial sums the handle's buffer holds
 
 // v * 2^20 truncated toward zero, for v >= 0 finite below 2^18, from the FP32
 // bits of v (exact integer arithmetic).
@@ -64,39 +30,117 @@ __device__ __forceinline__ unsigned long long to_fixed20(float v) {
     return m >> (-sh);
 }
 
-// Per-block sums of ||x_p - c_{index_p}||^2, each pixel's FP32 squared
-// distance truncated to units of 2^-20 and added as an integer, so the total
-// does not depend on the order of the additions.
-__global__ void __launch_bounds__(kMseThreads) k_mse_partial(
-    const uint8_t* __restrict__ rgb, int64_t n, int stride, const float4* __restrict__ centers,
-    int K, const uint8_t* __restrict__ index, unsigned long long* __restrict__ part, Ctrl* ctrl) {
-    __shared__ float4 s_c[WSM_MAX_K];
-    __shared__ unsigned long long s_red[kMseThreads / 32];
-    for (int k = threadIdx.x; k < K; k += blockDim.x) s_c[k] = centers[k];
-    __syncthreads();
-    unsigned long long acc = 0;
-    bool bad = false;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int k = index[p];
-        if (k >= K) {
-            bad = true;
+// ||x - c_k||^2 of a pixel key in units of 2^-20 (truncated), or a flag for
+// a label outside the palette.
+struct MseSum {
+    unsigned long long acc;
+    bool bad;
+};
+
+__device__ __forceinline__ void mse_add(MseSum& m, uint32_t key, int k, int K,
+                                        const float4* s_c) {
+    if (k >= K) {
+        m.bad = true;
+        return;
+    }
+    const float4 c = s_c[k];
+    m.acc += to_fixed20(sq3((float)(key >> 16), (float)((key >> 8) & 255u), (float)(key & 255u),
+                            c.x, c.y, c.z));
+}
+
+// One pass over the pixels of one image that thread t of nt handles.
+//   kGather: index[p] = lut[color of p] (0 for a skipped image);
+//   kMse:    the sum of ||x_p - c_{label_p}||^2, label_p the gathered label
+//            (kGather) or index[p], each pixel's FP32 squared distance
+//            truncated to units of 2^-20 and added as an integer, so that the
+//            total does not depend on the order of the additions.
+// Groups of 16 pixels go with vector loads (and one 16-byte index store or
+// load) when the pixels and the index image are 16-byte aligned, then the
+// last n % 16 pixels (or all of an unaligned image) one at a time.
+template <bool kGather, bool kMse>
+__device__ __forceinline__ MseSum pixel_pass(const uint8_t* __restrict__ rgb, int64_t n,
+                                             int stride, const uint8_t* __restrict__ lut,
+                                             uint8_t* __restrict__ index, const float4* s_c,
+                                             int K, bool skipped, int64_t t, int64_t nt) {
+    MseSum m = {0ull, false};
+    if (skipped && !kGather) return m;
+    int64_t done = 0;
+    if (vector_ok(rgb, index)) {
+        const int64_t ng = n / kGroup;
+        for (int64_t g = t; g < ng; g += nt) {
+            uint32_t lab[4] = {0u, 0u, 0u, 0u};
+            if (!skipped) {
+                uint32_t key[kGroup];
+                pixel_keys16(rgb, g, stride, key);
+                if (kGather) {
+#pragma unroll
+                    for (int j = 0; j < kGroup; ++j)
+                        lab[j >> 2] |= (uint32_t)__ldg(lut + key[j]) << (8 * (j & 3));
+                } else {
+                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(index) + g);
+                    lab[0] = v.x;
+                    lab[1] = v.y;
+                    lab[2] = v.z;
+                    lab[3] = v.w;
+                }
+                if (kMse) {
+#pragma unroll
+                    for (int j = 0; j < kGroup; ++j)
+                        mse_add(m, key[j], (lab[j >> 2] >> (8 * (j & 3))) & 255, K, s_c);
+                }
+            }
+            if (kGather)
+                reinterpret_cast<uint4*>(index)[g] = make_uint4(lab[0], lab[1], lab[2], lab[3]);
+        }
+        done = ng * kGroup;
+    }
+    for (int64_t p = done + t; p < n; p += nt) {
+        if (skipped) {
+            index[p] = 0;   // kGather only
             continue;
         }
         const uint32_t key = pixel_key(rgb, p, stride);
-        const float4 c = s_c[k];
-        acc += to_fixed20(sq3((float)((key >> 16) & 255u), (float)((key >> 8) & 255u),
-                              (float)(key & 255u), c.x, c.y, c.z));
+        const int k = kGather ? __ldg(lut + key) : index[p];
+        if (kGather) index[p] = (uint8_t)k;
+        if (kMse) mse_add(m, key, k, K, s_c);
     }
-    if (bad) atomicOr(&ctrl->status, ST_BAD_LABEL);
+    return m;
+}
+
+// The block's sum of acc over its threads (thread 0 returns it).
+__device__ __forceinline__ unsigned long long block_sum(unsigned long long acc) {
+    __shared__ unsigned long long s_red[kPixThreads / 32];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < kMseThreads / 32; ++w) t += s_red[w];
-        part[blockIdx.x] = t;
-    }
+    unsigned long long t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kPixThreads / 32; ++w) t += s_red[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(kPixThreads) k_gather(const uint8_t* __restrict__ rgb,
+                                                        int64_t n, int stride,
+                                                        const uint8_t* __restrict__ lut,
+                                                        uint8_t* __restrict__ index) {
+    pixel_pass<true, false>(rgb, n, stride, lut, index, nullptr, 0, false,
+                            (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                            (int64_t)gridDim.x * blockDim.x);
+}
+
+// Per-block sums of the squared errors of one image's pixels.
+__global__ void __launch_bounds__(kPixThreads) k_mse_partial(
+    const uint8_t* __restrict__ rgb, int64_t n, int stride, const float4* __restrict__ centers,
+    int K, const uint8_t* __restrict__ index, unsigned long long* __restrict__ part, Ctrl* ctrl) {
+    __shared__ float4 s_c[WSM_MAX_K];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) s_c[k] = centers[k];
+    __syncthreads();
+    const MseSum m = pixel_pass<false, true>(
+        rgb, n, stride, nullptr, const_cast<uint8_t*>(index), s_c, K, false,
+        (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+    if (m.bad) atomicOr(&ctrl->status, ST_BAD_LABEL);
+    const unsigned long long t = block_sum(m.acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // One warp adds the block sums and writes MSE = total * 2^-20 / N.
@@ -112,66 +156,51 @@ __global__ void k_mse_final(const unsigned long long* __restrict__ part, int npa
     }
 }
 
-// The images of one distortion launch: image i owns the partial-sum blocks
-// [first_blk[i], first_blk[i+1]).
-struct MseItems {
+// The images of one pixel pass over a batch (gather or MSE): image i owns
+// the blocks [first_blk[i], first_blk[i+1]).
+struct PixelItems {
     int n_items;
     int first_blk[kMaxBatch + 1];
     const uint8_t* rgb[kMaxBatch];
+    uint8_t* index[kMaxBatch];
     int64_t n[kMaxBatch];
     int stride[kMaxBatch];
-    const float4* centers[kMaxBatch];
     int K[kMaxBatch];
-    const uint8_t* index[kMaxBatch];
-    double* out[kMaxBatch];     // MSE (device), always written
-    double* user[kMaxBatch];    // MSE (device), a caller's copy, may be null
-    unsigned long long* part;   // one partial sum per block of the launch
+    const uint8_t* lut[kMaxBatch];      // the image's color->label table (gather)
+    const float4* centers[kMaxBatch];   // (MSE)
+    double* out[kMaxBatch];             // MSE (device), always written
+    double* user[kMaxBatch];            // MSE (device), a caller's copy, may be null
+    unsigned long long* part;           // one partial sum per block of the launch
     unsigned* status;
-    const int64_t* n_dev;       // if set: an image with n_dev[i] < K[i] was skipped (MSE 0)
+    const int64_t* n_dev;   // [n_items] or null: an image with N' < K was skipped
+                            // (index 0, MSE 0)
 };
 
-// Per-block fixed-point sums as in k_mse_partial, for the image owning the block.
-__global__ void __launch_bounds__(kMseThreads)
-    k_mse_partial_batch(const __grid_constant__ MseItems B) {
-    __shared__ float4 s_c[WSM_MAX_K];
-    __shared__ unsigned long long s_red[kMseThreads / 32];
+template <bool kGather, bool kMse>
+__global__ void __launch_bounds__(kPixThreads)
+    k_pixels_batch(const __grid_constant__ PixelItems B) {
+    __shared__ float4 s_c[kMse ? WSM_MAX_K : 1];
     const int i = item_of_block(B.first_blk, B.n_items, blockIdx.x);
     const int g = blockIdx.x - B.first_blk[i], G = B.first_blk[i + 1] - B.first_blk[i];
     const int K = B.K[i];
-    const uint8_t* rgb = B.rgb[i];
-    const uint8_t* index = B.index[i];
-    const int64_t n = B.n[i];
-    const int stride = B.stride[i];
     const bool skipped = B.n_dev && B.n_dev[i] < K;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) s_c[k] = B.centers[i][k];
-    __syncthreads();
-    unsigned long long acc = 0;
-    bool bad = false;
-    for (int64_t p = (int64_t)g * blockDim.x + threadIdx.x; !skipped && p < n;
-         p += (int64_t)G * blockDim.x) {
-        const int k = index[p];
-        if (k >= K) {
-            bad = true;
-            continue;
-        }
-        const uint32_t key = pixel_key(rgb, p, stride);
-        const float4 c = s_c[k];
-        acc += to_fixed20(sq3((float)((key >> 16) & 255u), (float)((key >> 8) & 255u),
-                              (float)(key & 255u), c.x, c.y, c.z));
+    if (kMse) {
+        for (int k = threadIdx.x; k < K; k += blockDim.x) s_c[k] = B.centers[i][k];
+        __syncthreads();
     }
-    if (bad) atomicOr(B.status, ST_BAD_LABEL);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < kMseThreads / 32; ++w) t += s_red[w];
-        B.part[blockIdx.x] = t;
+    const MseSum m = pixel_pass<kGather, kMse>(B.rgb[i], B.n[i], B.stride[i], B.lut[i],
+                                               B.index[i], s_c, K, skipped,
+                                               (int64_t)g * blockDim.x + threadIdx.x,
+                                               (int64_t)G * blockDim.x);
+    if (kMse) {
+        if (m.bad) atomicOr(B.status, ST_BAD_LABEL);
+        const unsigned long long t = block_sum(m.acc);
+        if (threadIdx.x == 0) B.part[blockIdx.x] = t;
     }
 }
 
 // One warp per image adds its blocks' sums and writes MSE = total * 2^-20 / N.
-__global__ void k_mse_final_batch(const __grid_constant__ MseItems B) {
+__global__ void k_mse_final_batch(const __grid_constant__ PixelItems B) {
     const int i = blockIdx.x;
     unsigned long long t = 0;
     for (int q = B.first_blk[i] + threadIdx.x; q < B.first_blk[i + 1]; q += 32) t += B.part[q];
@@ -183,77 +212,64 @@ __global__ void k_mse_final_batch(const __grid_constant__ MseItems B) {
     }
 }
 
-// The final assignment and the gather of n_items images (item i in slot i):
-// per kMaxBatch images one persistent launch in map mode and one gather.
-int map_items(wsm_handle* h, const wsm_item* items, int n_items, const int64_t* n_dev,
+// The final assignment of n_items images (item i in slot i): labels of the
+// unique colors and the slot's color->label table (and, with sse, the
+// slot's squared-error sum), per kMaxBatch images one persistent launch in
+// map mode.
+int map_items(wsm_handle* h, const wsm_item* items, int n_items, const int64_t* n_dev, bool sse,
               cudaStream_t s) {
     for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
         const int m = std::min(kMaxBatch, n_items - i0);
-        int rc = launch_map_items(h, items + i0, m, i0, n_dev, s);
+        int rc = launch_map_items(h, items + i0, m, i0, n_dev, sse, s);
         if (rc != WSM_OK) return rc;
-        GatherBatch B;
-        B.n_items = m;
-        B.lut = h->lut;
-        B.n_dev = n_dev;
-        int64_t total = 0;
-        for (int q = 0; q < m; ++q) total += items[i0 + q].n_pixels;
-        const int64_t budget = (int64_t)h->sms * 16;
-        B.first_blk[0] = 0;
-        for (int q = 0; q < m; ++q) {
-            const wsm_item& it = items[i0 + q];
-            B.rgb[q] = it.d_rgb;
-            B.index[q] = it.d_index;
-            B.n[q] = it.n_pixels;
-            B.stride[q] = it.pixel_stride;
-            B.slot[q] = i0 + q;
-            B.K[q] = it.K;
-            const int64_t want = (it.n_pixels + 255) / 256;
-            const int64_t share =
-                std::max<int64_t>(1, budget * it.n_pixels / std::max<int64_t>(total, 1));
-            B.first_blk[q + 1] = B.first_blk[q] + (int)std::min(want, share);
-        }
-        k_gather_batch<<<B.first_blk[m], 256, 0, s>>>(B);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "gather launch");
     }
     return WSM_OK;
 }
 
-// Eq. 2 for n_items images (item i's MSE to batch_mse[i] and, if d_mse is
-// given, d_mse[i]): per kMaxBatch images one pair of launches.  With n_dev,
-// an image skipped for N' < K gets MSE 0.
-int distortion_items(wsm_handle* h, const wsm_item* items, int n_items, double* d_mse,
-                     const int64_t* n_dev, cudaStream_t s) {
+// A pass over the pixels of n_items images (item i in slot i), per kMaxBatch
+// images one launch: the index images through the slots' tables (gather,
+// after map_items), or Eq. 2 from the index images (item i's MSE to
+// batch_mse[i] and, if d_mse is given, d_mse[i]; plus one launch of the
+// final sums).
+int pixel_items(wsm_handle* h, const wsm_item* items, int n_items, bool gather, double* d_mse,
+                const int64_t* n_dev, cudaStream_t s) {
     for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
-        MseItems B;
+        PixelItems B;
         B.n_items = std::min(kMaxBatch, n_items - i0);
         B.n_dev = n_dev ? n_dev + i0 : nullptr;
         B.part = reinterpret_cast<unsigned long long*>(h->mse_part);
         B.status = &h->ctrl->status;
         int64_t total = 0;
         for (int q = 0; q < B.n_items; ++q) total += items[i0 + q].n_pixels;
-        // at most 4 blocks per SM in all (and no more than the partial-sum
-        // buffer holds), split in proportion to pixels, >= 1 block per image
-        const int64_t budget = std::min<int64_t>(kMseMaxBlocks - kMaxBatch, 4 * (int64_t)h->sms);
+        // at most 6 blocks of 256 per SM in all (and no more partial sums than
+        // the buffer holds), split in proportion to pixels, >= 1 block per
+        // image, one 16-pixel group per thread
+        const int64_t budget = std::min<int64_t>(kMseMaxBlocks - kMaxBatch, 6 * (int64_t)h->sms);
         B.first_blk[0] = 0;
         for (int q = 0; q < B.n_items; ++q) {
             const wsm_item& it = items[i0 + q];
             B.rgb[q] = it.d_rgb;
+            B.index[q] = it.d_index;
             B.n[q] = it.n_pixels;
             B.stride[q] = it.pixel_stride;
-            B.centers[q] = reinterpret_cast<const float4*>(it.d_centers);
             B.K[q] = it.K;
-            B.index[q] = it.d_index;
+            B.lut[q] = h->lut + (size_t)(i0 + q) * kHistBins;
+            B.centers[q] = reinterpret_cast<const float4*>(it.d_centers);
             B.out[q] = h->batch_mse + i0 + q;
             B.user[q] = d_mse ? d_mse + i0 + q : nullptr;
-            const int64_t want = (it.n_pixels + 4 * kMseThreads - 1) / (4 * kMseThreads);
+            const int64_t want = (it.n_pixels + kGroup * kPixThreads - 1) / (kGroup * kPixThreads);
             const int64_t share = std::max<int64_t>(1, budget * it.n_pixels / total);
             B.first_blk[q + 1] = B.first_blk[q] + (int)std::min(want, share);
         }
-        k_mse_partial_batch<<<B.first_blk[B.n_items], kMseThreads, 0, s>>>(B);
-        k_mse_final_batch<<<B.n_items, 32, 0, s>>>(B);
+        const int grid = B.first_blk[B.n_items];
+        if (gather) {
+            k_pixels_batch<true, false><<<grid, kPixThreads, 0, s>>>(B);
+        } else {
+            k_pixels_batch<false, true><<<grid, kPixThreads, 0, s>>>(B);
+            k_mse_final_batch<<<B.n_items, 32, 0, s>>>(B);
+        }
         cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "distortion launch");
+        if (e != cudaSuccess) return cuda_fail(e, "pixel pass launch");
     }
     return WSM_OK;
 }
@@ -283,8 +299,8 @@ extern "C" int wsm_map(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, in
     rc = launch_sortmeans(h, true, d_colors, nullptr, n_unique, K, const_cast<float*>(d_centers),
                           d_labels, 1, 0.0, s);
     if (rc != WSM_OK) return rc;
-    int64_t blocks = (n_pixels + 255) / 256;
-    int grid = (int)std::min<int64_t>(blocks, (int64_t)h->sms * 16);
+    int64_t blocks = (n_pixels + 256 * kGroup - 1) / (256 * kGroup);
+    int grid = (int)std::min<int64_t>(blocks, (int64_t)h->sms * 8);
     k_gather<<<grid, 256, 0, s>>>(d_rgb, n_pixels, pixel_stride, h->lut, d_index);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "gather launch");
@@ -302,7 +318,9 @@ extern "C" int wsm_map_batch(wsm_handle* h, const wsm_item* items, int n_items,
         rc = check_item(h, items[i], true, false);
         if (rc != WSM_OK) return rc;
     }
-    return map_items(h, items, n_items, nullptr, (cudaStream_t)stream);
+    rc = map_items(h, items, n_items, nullptr, false, (cudaStream_t)stream);
+    if (rc != WSM_OK) return rc;
+    return pixel_items(h, items, n_items, true, nullptr, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels,
@@ -322,11 +340,11 @@ extern "C" int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pix
     if (pixel_stride == 4 && ((uintptr_t)d_rgb & 3))
         return fail(WSM_E_INVAL, "4-byte pixels must be 4-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
-    int64_t want = (n_pixels + 4 * kMseThreads - 1) / (4 * kMseThreads);
+    int64_t want = (n_pixels + kGroup * kPixThreads - 1) / (kGroup * kPixThreads);
     int grid = (int)std::max<int64_t>(
-        1, std::min<int64_t>(want, std::min(kMseMaxBlocks, 4 * h->sms)));
+        1, std::min<int64_t>(want, std::min(kMseMaxBlocks, 6 * h->sms)));
     unsigned long long* part = reinterpret_cast<unsigned long long*>(h->mse_part);
-    k_mse_partial<<<grid, kMseThreads, 0, s>>>(d_rgb, n_pixels, pixel_stride,
+    k_mse_partial<<<grid, kPixThreads, 0, s>>>(d_rgb, n_pixels, pixel_stride,
                                                 reinterpret_cast<const float4*>(d_centers), K,
                                                 d_index, part, h->ctrl);
     k_mse_final<<<1, 32, 0, s>>>(part, grid, n_pixels, h->mse_part + kMseMaxBlocks, d_mse);
@@ -366,7 +384,7 @@ extern "C" int wsm_distortion_batch(wsm_handle* h, const wsm_item* items, int n_
     }
     if (n_items == 0) return WSM_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    rc = distortion_items(h, items, n_items, d_mse, nullptr, s);
+    rc = pixel_items(h, items, n_items, false, d_mse, nullptr, s);
     if (rc != WSM_OK) return rc;
     if (mse) {
         cudaError_t e = cudaMemcpyAsync(h->host_mse, h->batch_mse, sizeof(double) * n_items,

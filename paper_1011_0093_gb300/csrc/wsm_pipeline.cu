@@ -30,6 +30,38 @@ __global__ void k_outputs(int n_items, const int64_t* __restrict__ nu,
     }
 }
 
+// Eq. 2 of image i from its final assignment: MSE = map_sse * 2^-20 / n.
+// The assignment summed, over the unique colors, count * (squared distance
+// to the assigned center truncated to 2^-20 units), with the distances the
+// per-pixel MSE computes, so this equals that MSE bit for bit.
+struct MapMse {
+    int n_items;
+    int64_t n[kMaxBatch];
+};
+
+__global__ void k_mse_from_map(const __grid_constant__ MapMse M, const Ctrl* __restrict__ ctrl,
+                               double* __restrict__ out, double* __restrict__ user) {
+    for (int i = threadIdx.x; i < M.n_items; i += blockDim.x) {
+        const double m = (double)ctrl[i].map_sse * (1.0 / 1048576.0) / (double)M.n[i];
+        out[i] = m;
+        if (user) user[i] = m;
+    }
+}
+
+static int mse_from_map(wsm_handle* h, const wsm_item* items, int n_items, double* d_mse,
+                        cudaStream_t s) {
+    for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
+        MapMse M;
+        M.n_items = std::min(kMaxBatch, n_items - i0);
+        for (int q = 0; q < M.n_items; ++q) M.n[q] = items[i0 + q].n_pixels;
+        k_mse_from_map<<<1, 64, 0, s>>>(M, h->slot_ctrl + i0, h->batch_mse + i0,
+                                        d_mse ? d_mse + i0 : nullptr);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "MSE launch");
+    }
+    return WSM_OK;
+}
+
 static int check_batch(wsm_handle* h, const wsm_item* items, int n_items, const uint64_t* seeds,
                        int max_iter) {
     int rc = check_handle(h);
@@ -101,9 +133,12 @@ extern "C" int wsm_quantize_batch_stages(wsm_handle* h, const wsm_item* items, i
             if (e != cudaSuccess) rc = cuda_fail(e, "output launch");
         }
     }
-    if (rc == WSM_OK && (stages & WSM_STAGE_MAP)) rc = map_items(h, items, n_items, h->batch_nu, s);
+    if (rc == WSM_OK && (stages & WSM_STAGE_MAP))
+        rc = map_items(h, items, n_items, h->batch_nu, true, s);
+    if (rc == WSM_OK && (stages & WSM_STAGE_INDEX))
+        rc = pixel_items(h, items, n_items, true, nullptr, h->batch_nu, s);
     if (rc == WSM_OK && (stages & WSM_STAGE_DISTORTION))
-        rc = distortion_items(h, items, n_items, d_mse, h->batch_nu, s);
+        rc = mse_from_map(h, items, n_items, d_mse, s);
     return rc;
 }
 

@@ -72,7 +72,7 @@ def gaps(colors, centers):
     return second - best
 
 
-# ---- a1: unique colors and counts -----------------------------------------------
+# ---- unique colors and counts --------------------------------------------------
 
 @pytest.mark.parametrize("case", ["plain256", "sweep0", "sweep3", "sweep7", "ragged", "stride4",
                                   "single_pixel", "one_color", "tiny_levels", "wide"])
@@ -136,7 +136,7 @@ def test_reduce_capacity_overflow_then_recovers(wsm, h):
     assert np.array_equal(c.cpu().numpy(), oc) and np.array_equal(n.cpu().numpy(), on)
 
 
-# ---- a2: initial centers ---------------------------------------------------------
+# ---- initial centers -------------------------------------------------------------
 
 @pytest.mark.parametrize("K,seed", [(1, 0), (16, 0), (32, 5), (256, 123456789), (256, 2**64 - 1)])
 def test_init_matches_oracle(wsm, h, K, seed):
@@ -164,7 +164,7 @@ def test_init_all_colors_and_too_many(wsm, h):
                                                       device="cuda"), labels)
 
 
-# ---- a3-a6: the Sort-Means iterations, teacher-forced ----------------------------
+# ---- the Sort-Means iterations, teacher-forced ----------------------------------
 
 def check_pass(colors, counts, c, lab, got_labels, got_centers, got_S, got_W, got_sse,
                got_ev, it, paper_scan=True):
@@ -320,7 +320,7 @@ def test_whole_path_sweep512_fixed10(wsm, h, s):
         compare_whole_path(wsm, h, img, K, 1000 * s + K, 10, 0.0)
 
 
-# ---- a7, a8: mapping and distortion -----------------------------------------------
+# ---- mapping and distortion -------------------------------------------------------
 
 def test_map_and_distortion_given_labels(wsm, h):
     """wsm_map with its input memberships already final: the index image is the
@@ -352,6 +352,43 @@ def test_map_and_distortion_given_labels(wsm, h):
     wsm.wsm_map(h, dev(img4), dev(colors), len(colors), centers, K, labels, index4)
     assert torch.equal(index4, index)
     assert wsm.wsm_distortion(h, dev(img4), centers, K, index4) == m
+
+
+def test_unaligned_buffers_take_the_byte_path(wsm, h):
+    """Pixels and index images that do not start on a 16-byte boundary (the
+    kernels then read one pixel at a time) give the same unique colors, index
+    image and MSE as 16-byte-aligned copies; n % 16 != 0 covers the tail of
+    the vector path too."""
+    img = synth.image(173, 97, 21, 6)                     # 16781 pixels, 16781 % 16 == 13
+    n = img.shape[0] * img.shape[1]
+    K = 32
+    c_al, w_al, nu = gpu_unique(wsm, h, img)
+    for off in (1, 3, 8):
+        buf = torch.zeros(3 * n + 16, dtype=torch.uint8, device="cuda")
+        rgb = buf[off:off + 3 * n].view(img.shape)
+        rgb.copy_(dev(img))
+        assert rgb.data_ptr() % 16 == off % 16
+        colors = torch.empty(n, dtype=torch.uint32, device="cuda")
+        counts = torch.empty(n, dtype=torch.uint32, device="cuda")
+        assert wsm.wsm_reduce(h, rgb, colors, counts) == nu
+        assert torch.equal(colors[:nu], c_al) and torch.equal(counts[:nu], w_al)
+    colors, counts = oracle.unique(img)
+    c0, lab0 = oracle.init(colors, K, 5)
+    r = oracle.run(colors, counts, c0, lab0, 5, 0.0)
+    pal = dev(pad4(r["centers"].astype(np.float32)))
+    labels = dev(r["labels"].astype(np.uint8))
+    ref_index = torch.empty(img.shape[:2], dtype=torch.uint8, device="cuda")
+    wsm.wsm_map(h, dev(img), dev(colors), len(colors), pal, K, labels, ref_index)
+    ref_mse = wsm.wsm_distortion(h, dev(img), pal, K, ref_index)
+    for off in (1, 5):
+        buf = torch.zeros(3 * n + 16, dtype=torch.uint8, device="cuda")
+        rgb = buf[off:off + 3 * n].view(img.shape)
+        rgb.copy_(dev(img))
+        ibuf = torch.zeros(n + 16, dtype=torch.uint8, device="cuda")
+        index = ibuf[off:off + n].view(img.shape[:2])
+        wsm.wsm_map(h, rgb, dev(colors), len(colors), pal, K, labels, index)
+        assert torch.equal(index, ref_index)
+        assert wsm.wsm_distortion(h, rgb, pal, K, index) == ref_mse
 
 
 # ---- edge cases -------------------------------------------------------------------

@@ -191,12 +191,19 @@ def test_stages_in_separate_calls_and_graphs_equal_one_call(wsm):
     whole.run()
     whole.sync()
     parts = (wsm.STAGE_REDUCE | wsm.STAGE_INIT, wsm.STAGE_ITERATE,
-             wsm.STAGE_MAP | wsm.STAGE_DISTORTION)
+             wsm.STAGE_MAP | wsm.STAGE_INDEX | wsm.STAGE_DISTORTION)
     split = wsm.BatchPlan([i.shape for i in imgs], Ks, seeds, max_iter=10)
     split.load([torch.from_numpy(i) for i in imgs])
-    for stages in parts:
+    # every stage in a call of its own, the MSE last
+    for stages in (wsm.STAGE_REDUCE, wsm.STAGE_INIT, wsm.STAGE_ITERATE, wsm.STAGE_MAP,
+                   wsm.STAGE_INDEX, wsm.STAGE_DISTORTION):
         split.run(stages)
     split.sync()
+    # the MSE of the pipeline (from the final assignment) is the per-pixel
+    # MSE of the index images, bit for bit
+    per_pixel = wsm.wsm_distortion_batch(split.handle, split.images)
+    for q in range(len(imgs)):
+        assert per_pixel[q] == split.result(q)["mse"], q
     graphs = wsm.BatchPlan([i.shape for i in imgs], Ks, seeds, max_iter=10)
     graphs.load([torch.from_numpy(i) for i in imgs])
     graphs.capture(parts)
