@@ -63,9 +63,10 @@ UNIT = "assignments/s"
 L2_FLUSH_BYTES = 256 << 20
 # per step, all images together: hist24, scan_count, scan_emit (up to 16 images
 # per launch), init, the plan kernel, the sort-means launch and the output copy
-# for the iterations, the plan kernel, the map-mode sort-means launch and the
-# gather for the mapping, mse_partial and mse_final (up to 48 images per launch)
-KERNELS_PER_STEP = 12
+# for the iterations, the plan kernel, the map-mode sort-means launch (which
+# also sums the squared errors), the gather and the MSE kernel (up to 48
+# images per launch)
+KERNELS_PER_STEP = 11
 
 
 def workload(rank: int):
@@ -271,15 +272,19 @@ def run_gpu(args):
     it_events = []
 
     def step(record: bool):
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)] if record else None
-        plan.replay(0)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
         if record:
             e[0].record(stream)
-        plan.replay(1)
+        plan.replay(0)
         if record:
             e[1].record(stream)
-            it_events.append(e)
+        plan.replay(1)
+        if record:
+            e[2].record(stream)
         plan.replay(2)
+        if record:
+            e[3].record(stream)
+            it_events.append(e)
 
     for _ in range(args.warmup):
         step(False)
@@ -344,7 +349,10 @@ def run_gpu(args):
     plan.sync()
 
     # roofline of the persistent sort-means kernel, from the timed steps
-    it_ms = [e0.elapsed_time(e1) for e0, e1 in it_events]
+    it_ms = [e[1].elapsed_time(e[2]) for e in it_events]
+    graph_ms = {name: statistics.median(e[q].elapsed_time(e[q + 1]) for e in it_events)
+                for q, name in enumerate(("unique colors + init", "iterations",
+                                          "final assignment + mapping + MSE"))}
     achieved_tflops = 8.0 * sum(evaluated) * len(it_ms) / (sum(it_ms) * 1e-3) / 1e12
     pk, pk_kind = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -372,7 +380,8 @@ def run_gpu(args):
                        "images_per_s": len(images) * world * args.steps / (total_ms * 1e-3),
                        "images_per_s_e2e": len(images) * world * args.steps / (e2e_total * 1e-3),
                        "l2": "flushed between steps (256 MiB write)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "graph_ms_median": graph_ms},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "alu", "kernel": "k_sortmeans<iterate> (8 images per launch)",
