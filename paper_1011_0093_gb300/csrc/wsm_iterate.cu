@@ -103,8 +103,9 @@ __host__ __device__ inline int64_t group_want(int64_t n, int K, int threads) {
 }
 
 // Split `grid` blocks into one group per image: min(want, floor) each, the
-// rest in proportion to each image's want beyond that (every image gets at
-// least one; grid >= n_items), integer arithmetic only so that host and
+// floor at most kGroupFloor and at most half of the grid over the images,
+// the rest in proportion to each image's want beyond that (every image gets
+// at least one; grid >= n_items), integer arithmetic only so that host and
 // device derive the same split.  Returns the number of blocks used.
 __host__ __device__ inline int split_groups(const int64_t* want, int n_items, int grid,
                                             int* first_blk) {
@@ -116,9 +117,11 @@ __host__ __device__ inline int split_groups(const int64_t* want, int n_items, in
         return first_blk[n_items];
     }
     // every image first gets min(want, floor) blocks: a small image's group
-    // still has the warps for its row build and for the tail of its visits
-    const int64_t floor = (int64_t)grid / n_items < kGroupFloor ? (int64_t)grid / n_items
-                                                                : kGroupFloor;
+    // still has the warps for its row build and for the tail of its visits;
+    // the floors take at most half of the grid, so that with many images the
+    // large ones still get their share
+    const int64_t half = (int64_t)grid / (2 * n_items) > 1 ? (int64_t)grid / (2 * n_items) : 1;
+    const int64_t floor = half < kGroupFloor ? half : kGroupFloor;
     int64_t fixed = 0;
     for (int i = 0; i < n_items; ++i) fixed += want[i] < floor ? want[i] : floor;
     const int64_t left = grid - fixed, excess = total - fixed;
