@@ -315,21 +315,18 @@ def run_gpu(args):
     total_ms = sum(step_ms)
 
     # e2e through the public API from pinned host memory: pixels up, then the
-    # same replay, then index images, palettes and MSE down
+    # same replay, then index images, palettes and MSE down (one copy per
+    # field for all images: BatchPlan keeps each field in one buffer)
     e2e_ms = []
-    h2d = sum(im.numel() for im in h_imgs)
-    d2h = len(images) * (n + K_PALETTE * 16 + 8)
-    out_idx = [torch.empty((H, W), dtype=torch.uint8).pin_memory() for _ in images]
-    out_pal = [torch.empty((K_PALETTE, 4), dtype=torch.float32).pin_memory() for _ in images]
-    out_mse = torch.empty(len(images), dtype=torch.float64).pin_memory()
+    h_packed = plan.pack(images)
+    out = plan.host_outputs()
+    h2d = h_packed.numel()
+    d2h = sum(t.numel() * t.element_size() for t in out.values())
 
     def e2e_step():
-        plan.load(h_imgs)
+        plan.load(h_packed)
         plan.replay()
-        for s in range(len(images)):
-            out_idx[s].copy_(plan.images[s]["index"], non_blocking=True)
-            out_pal[s].copy_(plan.images[s]["centers"], non_blocking=True)
-        out_mse.copy_(plan.mse, non_blocking=True)
+        plan.fetch(out)
 
     for _ in range(max(args.warmup, 1)):
         e2e_step()
@@ -659,10 +656,9 @@ def run_batch(args):
         ms.append(a.elapsed_time(b))
     plan.sync()
     # end to end: pixels up from pinned host memory, index images, palettes and
-    # MSE back, around the same replay
-    out_idx = [torch.empty(im.shape[:2], dtype=torch.uint8).pin_memory() for im in images]
-    out_pal = torch.empty((n_img, K_PALETTE, 4), dtype=torch.float32).pin_memory()
-    out_mse = torch.empty(n_img, dtype=torch.float64).pin_memory()
+    # MSE back (one copy per field for all images), around the same replay
+    h_packed = plan.pack(images)
+    out = plan.host_outputs()
     e2e = []
     for _ in range(args.steps):
         flush.fill_(1)
@@ -670,12 +666,9 @@ def run_batch(args):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        plan.load(h_imgs)
+        plan.load(h_packed)
         plan.replay()
-        for q in range(n_img):
-            out_idx[q].copy_(plan.images[q]["index"], non_blocking=True)
-            out_pal[q].copy_(plan.images[q]["centers"], non_blocking=True)
-        out_mse.copy_(plan.mse, non_blocking=True)
+        plan.fetch(out)
         b.record(stream)
         b.synchronize()
         e2e.append(a.elapsed_time(b))
@@ -718,9 +711,9 @@ def run_batch(args):
                    "unique_colors_total": int(sum(n_unique)),
                    "l2": "flushed between steps (256 MiB write)"},
         "e2e": {"value": n_img / (statistics.median(e2e) * 1e-3), "unit": "images/s",
-                "h2d_bytes_per_step": int(sum(im.nbytes for im in images)),
-                "d2h_bytes_per_step": int(sum(im.shape[0] * im.shape[1] for im in images)
-                                          + n_img * (K_PALETTE * 16 + 8))},
+                "h2d_bytes_per_step": int(h_packed.numel()),
+                "d2h_bytes_per_step": int(sum(t.numel() * t.element_size()
+                                              for t in out.values()))},
         "sequential_one_image_path": {"ms": min(seq), "images_per_s": n_img / (min(seq) * 1e-3),
                                       "speedup": min(seq) / step_ms,
                                       "identical_results": bool(same)},

@@ -3,13 +3,28 @@
 into a CUDA graph, then replayed on new pixels.
 
 Only buffer management and argument marshalling live here; every step of
-the path runs in libwsm's CUDA kernels.
+the path runs in libwsm's CUDA kernels.  The pixels, index images and
+palettes of all images live in one device buffer each (every image's part
+256-byte aligned), so that loading a batch and reading its results take one
+copy per field instead of one per image.
 """
 from __future__ import annotations
 
 import torch
 
 from . import _native as N
+
+_ALIGN = 256   # bytes: each image's part of a shared buffer starts on this boundary
+
+
+def _offsets(nbytes):
+    """Start offsets (bytes) of consecutive parts of the given sizes, each
+    aligned to _ALIGN, and the total size."""
+    offs, at = [], 0
+    for b in nbytes:
+        offs.append(at)
+        at += (int(b) + _ALIGN - 1) // _ALIGN * _ALIGN
+    return offs, at
 
 
 class BatchPlan:
@@ -29,16 +44,24 @@ class BatchPlan:
         self.handle = handle if handle is not None else N.Handle(max(Ks), biggest, biggest)
         N.wsm_reserve_batch(self.handle, self.n_items)
         dev = self.device
+        self.shapes = [(int(h), int(w), int(c)) for h, w, c in shapes]
+        self._rgb_off, rgb_total = _offsets(h * w * c for h, w, c in self.shapes)
+        self._idx_off, idx_total = _offsets(h * w for h, w, _ in self.shapes)
+        self._pal_off, pal_total = _offsets(16 * k for k in Ks)
+        self.rgb_all = torch.zeros(rgb_total, dtype=torch.uint8, device=dev)
+        self.index_all = torch.zeros(idx_total, dtype=torch.uint8, device=dev)
+        self.centers_all = torch.zeros(pal_total // 4, dtype=torch.float32, device=dev)
         self.images = []
-        for (h, w, c), k in zip(shapes, Ks):
-            n = int(h) * int(w)
+        for q, ((h, w, c), k) in enumerate(zip(self.shapes, Ks)):
+            n = h * w
+            r0, i0, p0 = self._rgb_off[q], self._idx_off[q], self._pal_off[q] // 4
             self.images.append(dict(
-                rgb=torch.zeros((h, w, c), dtype=torch.uint8, device=dev), K=int(k),
+                rgb=self.rgb_all[r0:r0 + n * c].view(h, w, c), K=int(k),
                 colors=torch.empty(n, dtype=torch.uint32, device=dev),
                 counts=torch.empty(n, dtype=torch.uint32, device=dev),
-                centers=torch.zeros((k, 4), dtype=torch.float32, device=dev),
+                centers=self.centers_all[p0:p0 + 4 * k].view(k, 4),
                 labels=torch.empty(n, dtype=torch.uint8, device=dev),
-                index=torch.empty((h, w), dtype=torch.uint8, device=dev)))
+                index=self.index_all[i0:i0 + n].view(h, w)))
         self.n_unique = torch.zeros(self.n_items, dtype=torch.int64, device=dev)
         self.iters = torch.zeros(self.n_items, dtype=torch.int32, device=dev)
         self.mse = torch.zeros(self.n_items, dtype=torch.float64, device=dev)
@@ -47,11 +70,51 @@ class BatchPlan:
         self.graph = None
         self.graphs = []
 
+    def pack(self, images, pin: bool = True) -> torch.Tensor:
+        """A host buffer laid out like the device pixel buffer, holding the
+        given images (uint8 [H, W, C] arrays or tensors): load() copies it
+        in one transfer."""
+        buf = torch.zeros(self.rgb_all.numel(), dtype=torch.uint8)
+        if pin:
+            buf = buf.pin_memory()
+        for q, im in enumerate(images):
+            t = torch.as_tensor(im).reshape(-1)
+            buf[self._rgb_off[q]:self._rgb_off[q] + t.numel()].copy_(t)
+        return buf
+
     def load(self, images, non_blocking: bool = True):
-        """Copy new pixels (uint8 [H, W, C] tensors, host or device) into the
-        static input buffers, on the current stream."""
+        """Copy new pixels into the static input buffers, on the current
+        stream: a buffer from pack() in one copy, or a list of uint8
+        [H, W, C] tensors (host or device) one copy each."""
+        if isinstance(images, torch.Tensor) and images.dim() == 1:
+            self.rgb_all.copy_(images, non_blocking=non_blocking)
+            return
         for dst, src in zip((im["rgb"] for im in self.images), images):
             dst.copy_(torch.as_tensor(src), non_blocking=non_blocking)
+
+    def host_outputs(self, pin: bool = True) -> dict:
+        """Host buffers for fetch(): index images, palettes and MSE of all
+        images, laid out like the device buffers."""
+        def mk(t):
+            h = torch.empty(t.shape, dtype=t.dtype)
+            return h.pin_memory() if pin else h
+        return dict(index=mk(self.index_all), centers=mk(self.centers_all), mse=mk(self.mse))
+
+    def fetch(self, out: dict, non_blocking: bool = True):
+        """Copy the index images, palettes and MSE of all images into the
+        buffers of host_outputs(), one copy each, on the current stream;
+        image i's parts are at index_offset(i) and palette_offset(i)."""
+        out["index"].copy_(self.index_all, non_blocking=non_blocking)
+        out["centers"].copy_(self.centers_all, non_blocking=non_blocking)
+        out["mse"].copy_(self.mse, non_blocking=non_blocking)
+
+    def index_offset(self, i: int) -> int:
+        """Where image i's index image starts in index_all (bytes)."""
+        return self._idx_off[i]
+
+    def palette_offset(self, i: int) -> int:
+        """Where image i's palette starts in centers_all (floats)."""
+        return self._pal_off[i] // 4
 
     def run(self, stages: int = N.STAGE_ALL, stream=None):
         """Enqueue unique colors -> init -> iterations -> mapping -> MSE (or

@@ -231,3 +231,35 @@ def test_a_barrier_that_can_never_complete_times_out_and_the_handle_stays_usable
         q = wsm.quantize(torch.from_numpy(img).cuda(), 16, 1, max_iter=5, handle=h)
         ref = wsm.quantize(torch.from_numpy(img).cuda(), 16, 1, max_iter=5)
         assert torch.equal(q.centers, ref.centers) and torch.equal(q.index, ref.index)
+
+
+def test_packed_load_and_fetch_equal_per_image_copies(wsm):
+    """pack() + load() move all images' pixels in one copy and fetch() brings
+    every index image, palette and MSE back in one copy per field; the parts
+    sit at index_offset(i) / palette_offset(i) and equal the per-image
+    results."""
+    imgs, Ks = uneven_batch(6, seed0=3100)
+    seeds = [11 * q + 1 for q in range(len(imgs))]
+    a = wsm.BatchPlan([i.shape for i in imgs], Ks, seeds, max_iter=6)
+    a.load([torch.from_numpy(i) for i in imgs])
+    a.run()
+    a.sync()
+    b = wsm.BatchPlan([i.shape for i in imgs], Ks, seeds, max_iter=6)
+    packed = b.pack(imgs)
+    b.load(packed)
+    b.run()
+    out = b.host_outputs()
+    b.fetch(out)
+    b.sync()
+    for q, img in enumerate(imgs):
+        ra = a.result(q)
+        h, w = img.shape[:2]
+        K = Ks[q]
+        i0, p0 = b.index_offset(q), b.palette_offset(q)
+        assert i0 % 256 == 0 and (4 * p0) % 256 == 0
+        idx = out["index"][i0:i0 + h * w].view(h, w)
+        pal = out["centers"][p0:p0 + 4 * K].view(K, 4)
+        assert torch.equal(idx, ra["index"].cpu())
+        assert torch.equal(pal, ra["centers"].cpu())
+        assert float(out["mse"][q]) == ra["mse"]
+        assert torch.equal(b.images[q]["rgb"].cpu(), torch.from_numpy(img))
