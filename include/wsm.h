@@ -289,6 +289,28 @@ WSM_API int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels
                    const float* d_centers, int K, const uint8_t* d_index, double* d_mse,
                    double* mse, wsm_stream stream);
 
+/* Sec. 3.1: the palette as 8-bit colors.  Every FP32 center coordinate is
+ * rounded to the nearest integer, ties to even, and clamped to [0, 255].
+ * A quantized image stores such colors; the paper does not say whether its
+ * MSE uses them, so wsm_distortion on the FP32 centers gives the primary
+ * MSE and wsm_distortion on d_rounded the MSE of the 8-bit palette.
+ *   d_centers  device float [K][4] (x, y, z, unused), 16-byte aligned
+ *   d_palette  device uint8 [K][4] out (R, G, B, 0), may be NULL
+ *   d_rounded  device float [K][4] out (the same colors as floats, 4th 0),
+ *              16-byte aligned, may be NULL
+ * Asynchronous.  Errors: WSM_E_INVAL (K out of [1, 256], null or unaligned
+ * pointers). */
+WSM_API int wsm_round_palette(wsm_handle* h, const float* d_centers, int K, uint8_t* d_palette,
+                              float* d_rounded, wsm_stream stream);
+
+/* Measured FP32 throughput of this GPU, for the roofline of the assignment
+ * kernel (not part of the method): a kernel of independent FMA chains, 8
+ * blocks of 256 threads per SM, timed with CUDA events (best of `repeats`
+ * after one untimed launch).  Synchronises the stream.
+ *   tflops  host out: FP32 TFLOP/s (one FMA = 2 FLOP)
+ * Errors: WSM_E_INVAL (repeats out of [1, 20]), WSM_E_CUDA. */
+WSM_API int wsm_measure_fp32(wsm_handle* h, int repeats, double* tflops, wsm_stream stream);
+
 /* The whole path -- Sec. 2 unique colors, Algorithm 2 (initialisation,
  * Sort-Means iterations with the Sec. 3.2 stop rule), Sec. 1 final
  * assignment and pixel mapping, Eq. 2 MSE -- for n_items images, with no

@@ -294,6 +294,15 @@ def psnr(m: float) -> float:
     return float(_load().wsmo_psnr(m))
 
 
+def round_palette(palette) -> np.ndarray:
+    """The palette as 8-bit colors (Sec. 3.1: a quantized image stores 8-bit
+    colors; the paper does not say whether its MSE uses them, so this is the
+    secondary palette): every coordinate rounded to the nearest integer, ties
+    to even, clamped to [0, 255]; float64 [K, 3]."""
+    p = np.asarray(palette, np.float64)[:, :3]
+    return np.clip(np.rint(p), 0.0, 255.0)
+
+
 def distortion_grad(X, w, centers):
     """D(C, X) = sum w_i min_k ||x_i - c_k||^2 and its gradients (dC, dX)."""
     X = np.ascontiguousarray(X, np.float64)

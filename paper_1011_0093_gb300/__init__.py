@@ -17,6 +17,7 @@ from ._native import (MAX_K, MAX_PIXELS, STAGE_ALL, STAGE_DISTORTION, STAGE_INDE
                       wsm_init_batch, wsm_iterate, wsm_iterate_batch, wsm_iterate_noalloc,
                       wsm_iterate_stats, wsm_launch_shape, wsm_map, wsm_map_batch,
                       wsm_quantize_batch, wsm_reduce, wsm_reduce_batch, wsm_reserve_batch,
+                      wsm_measure_fp32, wsm_round_palette,
                       wsm_set_first_pass_start, wsm_set_grid_limit, wsm_set_launch_shape,
                       wsm_sync_status)
 from .batch import BatchPlan
@@ -28,7 +29,8 @@ __all__ = [
     "MAX_K", "MAX_PIXELS", "Handle", "WsmError", "lib",
     # one image, step by step
     "wsm_reduce", "wsm_init", "wsm_iterate", "wsm_iterate_stats", "wsm_iterate_noalloc",
-    "wsm_map", "wsm_distortion", "wsm_sync_status", "Quantized", "quantize",
+    "wsm_map", "wsm_distortion", "wsm_round_palette", "wsm_sync_status", "Quantized",
+    "quantize",
     # batches of images
     "wsm_reserve_batch", "wsm_reduce_batch", "wsm_init_batch", "wsm_iterate_batch",
     "wsm_map_batch", "wsm_distortion_batch", "quantize_batch",
@@ -36,7 +38,7 @@ __all__ = [
     "wsm_quantize_batch", "pipeline_items", "STAGE_REDUCE", "STAGE_INIT", "STAGE_ITERATE",
     "STAGE_MAP", "STAGE_INDEX", "STAGE_DISTORTION", "STAGE_ALL", "wsm_autotune_batch",
     "wsm_launch_shape", "wsm_set_launch_shape", "wsm_set_grid_limit", "wsm_set_first_pass_start",
-    "wsm_batch_stats", "BatchPlan",
+    "wsm_batch_stats", "BatchPlan", "wsm_measure_fp32",
     # serving
     "Server",
     # differentiable distortion

@@ -104,6 +104,8 @@ SIGNATURES = {
                                      _P, _P, _P, _P]),
     "wsm_distortion": (C.c_int, [_P, _P, _I64, C.c_int, _P, C.c_int, _P, _P,
                                  C.POINTER(C.c_double), _P]),
+    "wsm_round_palette": (C.c_int, [_P, _P, C.c_int, _P, _P, _P]),
+    "wsm_measure_fp32": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double), _P]),
 }
 
 
@@ -402,6 +404,25 @@ def wsm_distortion(h: Handle, rgb: torch.Tensor, centers: torch.Tensor, K: int,
                                 _dev(d_mse, torch.float64, "d_mse", 1),
                                 C.byref(m) if sync else None, _stream(stream)))
     return m.value if sync else None
+
+
+def wsm_measure_fp32(h: Handle, repeats: int = 3, stream=None) -> float:
+    """Measured FP32 TFLOP/s of this GPU (independent FMA chains)."""
+    v = C.c_double(0.0)
+    _check(lib().wsm_measure_fp32(h.ptr, int(repeats), C.byref(v), _stream(stream)))
+    return v.value
+
+
+def wsm_round_palette(h: Handle, centers: torch.Tensor, K: int, stream=None):
+    """The palette as 8-bit colors (ties to even, clamped): (uint8 [K, 4],
+    float32 [K, 4] of the same values, for wsm_distortion)."""
+    pal = torch.empty((K, 4), dtype=torch.uint8, device=centers.device)
+    rounded = torch.empty((K, 4), dtype=torch.float32, device=centers.device)
+    _check(lib().wsm_round_palette(h.ptr, _dev(centers, torch.float32, "centers", 4 * K), K,
+                                   _dev(pal, torch.uint8, "palette", 4 * K),
+                                   _dev(rounded, torch.float32, "rounded", 4 * K),
+                                   _stream(stream)))
+    return pal, rounded
 
 
 def _points(t: torch.Tensor, name: str) -> tuple[int, int]:

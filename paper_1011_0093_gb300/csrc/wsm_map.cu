@@ -274,6 +274,21 @@ int pixel_items(wsm_handle* h, const wsm_item* items, int n_items, bool gather, 
     return WSM_OK;
 }
 
+// The palette as 8-bit colors: each coordinate rounded to the nearest
+// integer (rintf: ties to even in the default rounding mode), clamped.
+__global__ void k_round_palette(const float4* __restrict__ centers, int K,
+                                uchar4* __restrict__ palette, float4* __restrict__ rounded) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        const float4 c = centers[k];
+        const float r = fminf(fmaxf(rintf(c.x), 0.f), 255.f);
+        const float g = fminf(fmaxf(rintf(c.y), 0.f), 255.f);
+        const float b = fminf(fmaxf(rintf(c.z), 0.f), 255.f);
+        if (palette) palette[k] = make_uchar4((unsigned char)r, (unsigned char)g,
+                                              (unsigned char)b, 0);
+        if (rounded) rounded[k] = make_float4(r, g, b, 0.f);
+    }
+}
+
 }  // namespace wsm
 
 using namespace wsm;
@@ -394,5 +409,21 @@ extern "C" int wsm_distortion_batch(wsm_handle* h, const wsm_item* items, int n_
         if (rc != WSM_OK) return rc;
         for (int i = 0; i < n_items; ++i) mse[i] = h->host_mse[i];
     }
+    return WSM_OK;
+}
+
+extern "C" int wsm_round_palette(wsm_handle* h, const float* d_centers, int K, uint8_t* d_palette,
+                                 float* d_rounded, wsm_stream stream) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (K < 1 || K > WSM_MAX_K) return fail(WSM_E_INVAL, "K out of [1, 256]");
+    if (!d_centers) return fail(WSM_E_INVAL, "null centers");
+    if (((uintptr_t)d_centers & 15) || ((uintptr_t)d_rounded & 15) || ((uintptr_t)d_palette & 3))
+        return fail(WSM_E_INVAL, "centers/rounded must be 16-byte, palette 4-byte aligned");
+    k_round_palette<<<(K + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const float4*>(d_centers), K, reinterpret_cast<uchar4*>(d_palette),
+        reinterpret_cast<float4*>(d_rounded));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "palette launch");
     return WSM_OK;
 }

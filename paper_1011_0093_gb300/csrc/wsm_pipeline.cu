@@ -92,6 +92,26 @@ __global__ void k_barrier_timeout(unsigned* counter, unsigned* status,
     grid_sync(counter, status, gridDim.x + 1, limit_ns);
 }
 
+// Independent FMA chains (kFmaChains per thread, no memory traffic in the
+// loop); the sum is stored only if it equals a value it cannot take, so the
+// chains stay live.
+constexpr int kFmaChains = 16;
+
+__global__ void __launch_bounds__(256) k_ffma(float b, float c, int iters, float* sink) {
+    float a[kFmaChains];
+#pragma unroll
+    for (int q = 0; q < kFmaChains; ++q) a[q] = (float)(threadIdx.x + q) * 1e-3f;
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int q = 0; q < kFmaChains; ++q) a[q] = fmaf(a[q], b, c);
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < kFmaChains; ++q) sum += a[q];
+    if (sum == -1.0f) *sink = sum;
+}
+
 }  // namespace wsm
 
 using namespace wsm;
@@ -265,4 +285,36 @@ extern "C" int wsm_autotune_batch(wsm_handle* h, const wsm_item* items, int n_it
     }
     h->iter_shape = best;
     return best;
+}
+
+extern "C" int wsm_measure_fp32(wsm_handle* h, int repeats, double* tflops, wsm_stream stream) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (repeats < 1 || repeats > 20) return fail(WSM_E_INVAL, "repeats must be in [1, 20]");
+    if (!tflops) return fail(WSM_E_INVAL, "null output");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = 8 * h->sms, threads = 256, iters = 32768;
+    float* sink = reinterpret_cast<float*>(h->mse_part);   // never written in practice
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    float best = -1.f;
+    for (int r = 0; r <= repeats && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(a, s);
+        if (e == cudaSuccess) {
+            k_ffma<<<blocks, threads, 0, s>>>(0.999999f, 1e-6f, iters, sink);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && r > 0 && (best < 0.f || ms < best)) best = ms;
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_fail(e, "FP32 measurement");
+    const double flop = 2.0 * kFmaChains * (double)iters * threads * blocks;
+    *tflops = flop / (best * 1e-3) / 1e12;
+    return WSM_OK;
 }

@@ -22,6 +22,8 @@ class Quantized:
     iters: int
     sse_trace: list
     mse: float | None
+    palette8: torch.Tensor | None = None   # uint8 [K, 4] 8-bit palette (ties to even), device
+    mse8: float | None = None               # Eq. 2 with the 8-bit palette
 
 
 def quantize(rgb: torch.Tensor, K: int, seed: int = 0, max_iter: int = 10, eps: float = 0.0,
@@ -29,7 +31,8 @@ def quantize(rgb: torch.Tensor, K: int, seed: int = 0, max_iter: int = 10, eps: 
     """Quantize one uint8 [H, W, 3|4] CUDA image to K colors.
 
     eps <= 0 runs exactly max_iter iterations (WSM); eps > 0 stops on the
-    relative SSE change (WSM-C, Sec. 3.2) or at max_iter.
+    relative SSE change (WSM-C, Sec. 3.2) or at max_iter.  With mse, the MSE
+    of Eq. 2 with the FP32 palette and with its 8-bit rounding.
     """
     if not rgb.is_cuda or rgb.dtype != torch.uint8 or rgb.dim() != 3:
         raise ValueError("rgb must be a uint8 CUDA tensor of shape [H, W, 3|4]")
@@ -49,8 +52,12 @@ def quantize(rgb: torch.Tensor, K: int, seed: int = 0, max_iter: int = 10, eps: 
                                  stream=stream)
     index = torch.empty((H, W), dtype=torch.uint8, device=dev)
     N.wsm_map(h, rgb, colors, nu, centers, K, labels, index, stream=stream)
-    m = N.wsm_distortion(h, rgb, centers, K, index, stream=stream) if mse else None
-    return Quantized(centers, index, colors, counts, labels, nu, iters, trace, m)
+    m = m8 = pal8 = None
+    if mse:
+        m = N.wsm_distortion(h, rgb, centers, K, index, stream=stream)
+        pal8, rounded = N.wsm_round_palette(h, centers, K, stream=stream)
+        m8 = N.wsm_distortion(h, rgb, rounded, K, index, stream=stream)
+    return Quantized(centers, index, colors, counts, labels, nu, iters, trace, m, pal8, m8)
 
 
 def quantize_batch(images: list, K: int, seeds: list, max_iter: int = 10, eps: float = 0.0,

@@ -58,6 +58,8 @@ def test_argument_errors_without_device(libwsm):
     assert libwsm.wsm_autotune_batch(None, None, 0, None, 10, 0.0, 1, None, None) == -1
     assert libwsm.wsm_set_grid_limit(None, 0) == -1
     assert libwsm.wsm_set_first_pass_start(None, 1) == -1
+    assert libwsm.wsm_round_palette(None, None, 4, None, None, None) == -1
+    assert libwsm.wsm_measure_fp32(None, 3, None, None) == -1
     assert libwsm.wsm_distortion_fwd(None, None, 3, None, 0, None, 3, 4, None, 0, None, None,
                                      None) == -1
     assert libwsm.wsm_iterate_noalloc(None, None, 1, 0, None, None, 1, 0.0, None, None,

@@ -391,6 +391,28 @@ def test_unaligned_buffers_take_the_byte_path(wsm, h):
         assert wsm.wsm_distortion(h, rgb, pal, K, index) == ref_mse
 
 
+def test_round_palette_and_the_mse_of_the_8bit_palette(wsm, h):
+    """The 8-bit palette is the oracle's rounding (ties to even, clamped) of
+    the same FP32 centers, bit for bit, and the MSE with it equals the
+    oracle's exactly (every squared distance is then an integer)."""
+    rng = np.random.default_rng(77)
+    K = 256
+    c = (rng.random((K, 4)) * 270 - 5).astype(np.float32)
+    c[:32, :3] = (rng.integers(0, 255, (32, 3)) + 0.5).astype(np.float32)   # exact ties
+    pal8, rounded = wsm.wsm_round_palette(h, dev(c), K)
+    expect = oracle.round_palette(c.astype(np.float64))
+    assert np.array_equal(pal8.cpu().numpy()[:, :3], expect.astype(np.uint8))
+    assert np.all(pal8.cpu().numpy()[:, 3] == 0)
+    assert np.array_equal(rounded.cpu().numpy()[:, :3], expect.astype(np.float32))
+    img = synth.image(211, 160, 31, 8)
+    q = wsm.quantize(dev(img), 64, seed=5, max_iter=10, handle=h)
+    pal = oracle.round_palette(q.centers.cpu().numpy().astype(np.float64))
+    assert np.array_equal(q.palette8.cpu().numpy()[:, :3], pal.astype(np.uint8))
+    ref = oracle.mse(img, pal, q.index.cpu().numpy())
+    assert q.mse8 == ref
+    assert q.mse8 >= 0.0 and abs(q.mse8 - q.mse) < 0.5 * 3 + 2 * (3 * q.mse) ** 0.5
+
+
 # ---- edge cases -------------------------------------------------------------------
 
 def test_k1_and_lossless(wsm, h):

@@ -334,6 +334,22 @@ def test_mse_psnr_closed_forms():
     assert oracle.psnr(255.0 ** 2) == 0.0
 
 
+def test_round_palette_ties_to_even_and_clamps():
+    """Round half to even (0.5 -> 0, 1.5 -> 2, 2.5 -> 2, 254.5 -> 254), plain
+    rounding elsewhere, clamping outside [0, 255]; the fourth column of a
+    [K, 4] palette is dropped."""
+    pal = np.array([[0.5, 1.5, 2.5, 9.0],
+                    [254.5, 255.49, 300.0, 9.0],
+                    [-0.2, 3.4999, 3.5001, 9.0],
+                    [127.5, 128.5, 0.0, 9.0]])
+    expect = np.array([[0, 2, 2], [254, 255, 255], [0, 3, 4], [128, 128, 0]], np.float64)
+    assert np.array_equal(oracle.round_palette(pal), expect)
+    # the MSE with the rounded palette of an image whose colors are the
+    # palette's rounded colors is 0
+    img = expect.astype(np.uint8)[None]
+    assert oracle.mse(img, oracle.round_palette(pal), np.arange(4, dtype=np.uint8)) == 0.0
+
+
 # ---- gradient of the weighted distortion ----------------------------------------
 
 def test_distortion_gradient_finite_differences():
