@@ -74,7 +74,8 @@ enum {
     WSM_E_CAPACITY = -6  /* more unique colors than the output arrays hold */
 };
 
-#define WSM_MAX_K 256
+#define WSM_MAX_K 256          /* largest palette with 8-bit memberships */
+#define WSM_MAX_K_WIDE 1024    /* largest palette of a wide handle (16-bit memberships) */
 #define WSM_MAX_PIXELS (1ll << 24)
 
 /* Message describing the calling thread's most recent failure ("" if none).
@@ -84,10 +85,17 @@ WSM_API const char* wsm_last_error(void);
 /* Create a handle for images of at most max_pixels pixels, at most
  * max_unique unique colors and palettes of at most max_K colors, on the
  * current device.  Allocates the scratch: a 2^24-bin uint32 color histogram
- * (64 MiB) with a one-bit-per-bin occupancy map (2 MiB), a 2^24-entry uint8
+ * (64 MiB) with a one-bit-per-bin occupancy map (2 MiB), a 2^24-entry
  * color->label table (16 MiB), the max_K x max_K sorted center tables and
- * the reduction and barrier words.  Errors: WSM_E_INVAL (limits out of
- * range), WSM_E_NOMEM, WSM_E_CUDA.  *h is NULL on failure. */
+ * the reduction and barrier words.
+ * Label width: with max_K <= 256 (WSM_MAX_K) every membership (d_labels),
+ * palette index (d_index) and table entry is a uint8; a handle with
+ * 256 < max_K <= 1024 (WSM_MAX_K_WIDE) is wide: they are uint16, and the
+ * calls that take d_labels or d_index read and write uint16 arrays (the
+ * pointer types below are void* for that reason).  The gradient calls, the
+ * server and wsm_iterate_noalloc keep palettes of at most 256 colors.
+ * Errors: WSM_E_INVAL (limits out of range), WSM_E_NOMEM, WSM_E_CUDA.  *h
+ * is NULL on failure. */
 WSM_API int wsm_create(wsm_handle** h, int max_K, int64_t max_pixels, int64_t max_unique);
 
 /* Free the handle and its scratch (synchronises the device first).
@@ -128,7 +136,7 @@ WSM_API int wsm_reduce(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, in
  *   d_colors   [n_unique]; d_centers [K][4] out; d_labels [n_unique] out
  * Errors: WSM_E_INVAL (K < 1, K > max_K, K > n_unique). */
 WSM_API int wsm_init(wsm_handle* h, const uint32_t* d_colors, int64_t n_unique, int K,
-                     uint64_t seed, float* d_centers, uint8_t* d_labels, wsm_stream stream);
+                     uint64_t seed, float* d_centers, void* d_labels, wsm_stream stream);
 
 /* Algorithm 2 with the Sec. 3.2 termination rule, in one persistent
  * cooperative launch.  Each iteration: the K x K squared center distances
@@ -151,7 +159,7 @@ WSM_API int wsm_init(wsm_handle* h, const uint32_t* d_colors, int64_t n_unique, 
  * Distances are FP32 on CUDA cores in difference form; sums are integers.
  * Errors: WSM_E_INVAL (K, sizes; label >= K found), WSM_E_TIMEOUT. */
 WSM_API int wsm_iterate(wsm_handle* h, const uint32_t* d_colors, const uint32_t* d_counts,
-                int64_t n_unique, int K, float* d_centers, uint8_t* d_labels, int max_iter,
+                int64_t n_unique, int K, float* d_centers, void* d_labels, int max_iter,
                 double eps, int* iters_done, double* sse_trace, wsm_stream stream);
 
 /* Diagnostics of the last wsm_iterate on this handle, valid until the next
@@ -181,8 +189,8 @@ typedef struct {
     uint32_t* d_counts;         /* [n_unique] (written by wsm_reduce_batch) */
     int64_t n_unique;
     float* d_centers;           /* [K][4], 16-byte aligned */
-    uint8_t* d_labels;          /* [n_unique] */
-    uint8_t* d_index;           /* [n_pixels] */
+    void* d_labels;             /* [n_unique] uint8 (uint16 with a wide handle) */
+    void* d_index;              /* [n_pixels] uint8 (uint16 with a wide handle) */
 } wsm_item;
 
 /* Reserve per-image scratch for batches of up to max_items images (about
@@ -276,7 +284,7 @@ WSM_API int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_coun
  * Errors: WSM_E_INVAL (sizes, K; label >= K found), WSM_E_TIMEOUT. */
 WSM_API int wsm_map(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, int pixel_stride,
             const uint32_t* d_colors, int64_t n_unique, const float* d_centers, int K,
-            uint8_t* d_labels, uint8_t* d_index, wsm_stream stream);
+            void* d_labels, void* d_index, wsm_stream stream);
 
 /* Sec. 3.1, Eq. 2: MSE = (1/N) sum_p ||x_p - c_{index_p}||^2 over the three
  * channels.  Each pixel's squared distance (FP32, difference form) is
@@ -286,7 +294,7 @@ WSM_API int wsm_map(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, int p
  *          given, the call synchronises).
  * Errors: WSM_E_INVAL (sizes, K; index >= K found). */
 WSM_API int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, int pixel_stride,
-                   const float* d_centers, int K, const uint8_t* d_index, double* d_mse,
+                   const float* d_centers, int K, const void* d_index, double* d_mse,
                    double* mse, wsm_stream stream);
 
 /* Sec. 3.1: the palette as 8-bit colors.  Every FP32 center coordinate is

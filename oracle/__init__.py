@@ -273,7 +273,7 @@ def map_pixels(rgb, colors, labels) -> np.ndarray:
     rgb, n, stride = _pixels(rgb)
     colors = np.ascontiguousarray(colors, np.uint32)
     lab = np.ascontiguousarray(labels, np.int32)
-    out = np.empty(n, np.uint8)
+    out = np.empty(n, np.int32)             # palette indices (K may exceed 256)
     if _load().wsmo_map(_ptr(rgb), n, stride, _ptr(colors), _ptr(lab), len(colors),
                         _ptr(out)) != 0:
         raise ValueError("pixel color missing from the unique list")
@@ -283,7 +283,7 @@ def map_pixels(rgb, colors, labels) -> np.ndarray:
 def mse(rgb, palette, index) -> float:
     rgb, n, stride = _pixels(rgb)
     pal = np.ascontiguousarray(palette, np.float64)
-    idx = np.ascontiguousarray(index, np.uint8).reshape(-1)
+    idx = np.ascontiguousarray(index, np.int32).reshape(-1)
     v = _load().wsmo_mse(_ptr(rgb), n, stride, _ptr(pal), pal.shape[0], _ptr(idx))
     if v < 0:
         raise ValueError("index out of palette range")

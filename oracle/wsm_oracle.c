@@ -373,7 +373,7 @@ double wsmo_kmeans_pixels_iteration(const uint8_t* rgb, int64_t n_pixels, int st
 /* index[p] = m[i] where x_i is the color of pixel p, found by binary search
  * in the ascending unique list.  Returns -1 if a color is missing. */
 int wsmo_map(const uint8_t* rgb, int64_t n_pixels, int stride, const uint32_t* colors,
-             const int32_t* labels, int64_t n_unique, uint8_t* index) {
+             const int32_t* labels, int64_t n_unique, int32_t* index) {
     for (int64_t p = 0; p < n_pixels; ++p) {
         const uint8_t* px = rgb + p * stride;
         uint32_t key = ((uint32_t)px[0] << 16) | ((uint32_t)px[1] << 8) | (uint32_t)px[2];
@@ -384,7 +384,7 @@ int wsmo_map(const uint8_t* rgb, int64_t n_pixels, int stride, const uint32_t* c
             if (colors[mid] < key) lo = mid + 1; else hi = mid - 1;
         }
         if (at < 0) return -1;
-        index[p] = (uint8_t)labels[at];
+        index[p] = labels[at];
     }
     return 0;
 }
@@ -393,11 +393,11 @@ int wsmo_map(const uint8_t* rgb, int64_t n_pixels, int stride, const uint32_t* c
  * palette color of the pixel's index (full squared norm over the three
  * channels, divided by the number of pixels only). */
 double wsmo_mse(const uint8_t* rgb, int64_t n_pixels, int stride, const double* palette, int K,
-                const uint8_t* index) {
+                const int32_t* index) {
     double acc = 0.0;
     for (int64_t p = 0; p < n_pixels; ++p) {
         int k = index[p];
-        if (k >= K) return -1.0;
+        if (k < 0 || k >= K) return -1.0;
         double x[3] = {rgb[p * stride], rgb[p * stride + 1], rgb[p * stride + 2]};
         acc += sqdist(x, palette + 3 * k);
     }

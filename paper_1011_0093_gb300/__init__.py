@@ -10,8 +10,9 @@ fixed batch's buffers and captures the whole path into a CUDA graph;
 ``distortion`` wraps the weighted distortion and its gradients as a
 torch.autograd.Function.  PyTorch only provides device memory and streams.
 """
-from ._native import (MAX_K, MAX_PIXELS, STAGE_ALL, STAGE_DISTORTION, STAGE_INDEX,
-                      STAGE_INIT, STAGE_ITERATE, STAGE_MAP, STAGE_REDUCE, Handle, WsmError, lib,
+from ._native import (MAX_K, MAX_K_WIDE, MAX_PIXELS, STAGE_ALL, STAGE_DISTORTION, STAGE_INDEX,
+                      STAGE_INIT, STAGE_ITERATE, STAGE_MAP, STAGE_REDUCE, Handle, WsmError,
+                      label_dtype, lib,
                       pipeline_items, wsm_autotune_batch, wsm_batch_stats, wsm_distortion,
                       wsm_distortion_batch, wsm_distortion_bwd, wsm_distortion_fwd, wsm_init,
                       wsm_init_batch, wsm_iterate, wsm_iterate_batch, wsm_iterate_noalloc,
@@ -26,7 +27,7 @@ from .distortion import WeightedDistortion, weighted_distortion
 from .quantize import Quantized, quantize, quantize_batch
 
 __all__ = [
-    "MAX_K", "MAX_PIXELS", "Handle", "WsmError", "lib",
+    "MAX_K", "MAX_K_WIDE", "MAX_PIXELS", "Handle", "WsmError", "label_dtype", "lib",
     # one image, step by step
     "wsm_reduce", "wsm_init", "wsm_iterate", "wsm_iterate_stats", "wsm_iterate_noalloc",
     "wsm_map", "wsm_distortion", "wsm_round_palette", "wsm_sync_status", "Quantized",

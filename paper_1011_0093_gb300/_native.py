@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libwsm.so")
 WSM_OK = 0
 ERRORS = {-1: "WSM_E_INVAL", -2: "WSM_E_NOMEM", -3: "WSM_E_CUDA", -4: "WSM_E_TIMEOUT",
           -5: "WSM_E_STATE", -6: "WSM_E_CAPACITY"}
-MAX_K = 256
+MAX_K = 256          # palettes with 8-bit memberships
+MAX_K_WIDE = 1024    # palettes of a wide handle (16-bit memberships)
 MAX_PIXELS = 1 << 24
 
 _lock = threading.Lock()
@@ -165,6 +166,23 @@ def _dev(t: torch.Tensor | None, dtype, name: str, min_numel: int = 0) -> int | 
     return t.data_ptr()
 
 
+def label_dtype(h) -> torch.dtype:
+    """The dtype of memberships and index images for handle h: uint8, or for
+    a wide handle (max_K > 256) int16, whose bits the library reads as
+    uint16 (palette indices stay below 1024)."""
+    return torch.int16 if int(h.max_K) > MAX_K else torch.uint8
+
+
+def _lab(t: torch.Tensor | None, wide: bool, name: str, min_numel: int = 0) -> int | None:
+    """A membership or index array: uint8, or for a wide handle int16/uint16."""
+    if t is None:
+        return None
+    ok = (torch.int16, getattr(torch, "uint16", torch.int16)) if wide else (torch.uint8,)
+    if t.dtype not in ok:
+        raise ValueError(f"{name} must be {ok[0]} for this handle, got {t.dtype}")
+    return _dev(t, t.dtype, name, min_numel)
+
+
 def _pixels(rgb: torch.Tensor) -> tuple[int, int]:
     stride = rgb.shape[-1]
     if stride not in (3, 4):
@@ -181,6 +199,7 @@ class Handle:
                                 int(max_unique if max_unique is not None else max_pixels)))
         self.ptr = h.value
         self.max_K = int(max_K)
+        self.wide = self.max_K > MAX_K      # 16-bit memberships and index images
         self.max_pixels = int(max_pixels)
         self.max_unique = int(max_unique if max_unique is not None else max_pixels)
 
@@ -224,7 +243,7 @@ def wsm_init(h: Handle, colors: torch.Tensor, n_unique: int, K: int, seed: int,
              centers: torch.Tensor, labels: torch.Tensor, stream=None):
     _check(lib().wsm_init(h.ptr, _dev(colors, torch.uint32, "colors", n_unique), n_unique, K,
                           seed & (2 ** 64 - 1), _dev(centers, torch.float32, "centers", 4 * K),
-                          _dev(labels, torch.uint8, "labels", n_unique), _stream(stream)))
+                          _lab(labels, h.wide, "labels", n_unique), _stream(stream)))
 
 
 def wsm_iterate(h: Handle, colors: torch.Tensor, counts: torch.Tensor, n_unique: int, K: int,
@@ -236,7 +255,7 @@ def wsm_iterate(h: Handle, colors: torch.Tensor, counts: torch.Tensor, n_unique:
     _check(lib().wsm_iterate(h.ptr, _dev(colors, torch.uint32, "colors", n_unique),
                              _dev(counts, torch.uint32, "counts", n_unique), n_unique, K,
                              _dev(centers, torch.float32, "centers", 4 * K),
-                             _dev(labels, torch.uint8, "labels", n_unique), max_iter, float(eps),
+                             _lab(labels, h.wide, "labels", n_unique), max_iter, float(eps),
                              C.byref(it) if sync else None,
                              C.cast(trace, C.c_void_p) if sync else None, _stream(stream)))
     if not sync:
@@ -284,15 +303,15 @@ def wsm_map(h: Handle, rgb: torch.Tensor, colors: torch.Tensor, n_unique: int,
     _check(lib().wsm_map(h.ptr, _dev(rgb, torch.uint8, "rgb"), n, stride,
                          _dev(colors, torch.uint32, "colors", n_unique), n_unique,
                          _dev(centers, torch.float32, "centers", 4 * K), K,
-                         _dev(labels, torch.uint8, "labels", n_unique),
-                         _dev(index, torch.uint8, "index", n), _stream(stream)))
+                         _lab(labels, h.wide, "labels", n_unique),
+                         _lab(index, h.wide, "index", n), _stream(stream)))
 
 
 def wsm_reserve_batch(h: Handle, max_items: int):
     _check(lib().wsm_reserve_batch(h.ptr, int(max_items)))
 
 
-def _items(images: list[dict], need_pixels: bool, need_counts: bool):
+def _items(images: list[dict], need_pixels: bool, need_counts: bool, wide: bool = False):
     """Marshal dicts with tensors (rgb, colors, counts, n_unique, K, centers,
     labels, index) into a wsm_item array."""
     arr = (WsmItem * max(len(images), 1))()
@@ -303,7 +322,7 @@ def _items(images: list[dict], need_pixels: bool, need_counts: bool):
         it.n_unique = nu
         it.d_colors = _dev(im["colors"], torch.uint32, "colors", nu)
         it.d_centers = _dev(im["centers"], torch.float32, "centers", 4 * K)
-        it.d_labels = _dev(im["labels"], torch.uint8, "labels", nu)
+        it.d_labels = _lab(im["labels"], wide, "labels", nu)
         if need_counts:
             it.d_counts = _dev(im["counts"], torch.uint32, "counts", nu)
         if need_pixels:
@@ -311,14 +330,14 @@ def _items(images: list[dict], need_pixels: bool, need_counts: bool):
             it.d_rgb = _dev(im["rgb"], torch.uint8, "rgb")
             it.n_pixels = n
             it.pixel_stride = stride
-            it.d_index = _dev(im["index"], torch.uint8, "index", n)
+            it.d_index = _lab(im["index"], wide, "index", n)
     return arr
 
 
 def wsm_iterate_batch(h: Handle, images: list[dict], max_iter: int, eps: float,
                       sync: bool = True, stream=None):
     """Iterate every image of the batch; returns the iteration counts if sync."""
-    arr = _items(images, False, True)
+    arr = _items(images, False, True, h.wide)
     done = (C.c_int * max(len(images), 1))()
     _check(lib().wsm_iterate_batch(h.ptr, C.cast(arr, C.c_void_p), len(images), max_iter,
                                    float(eps), C.cast(done, C.c_void_p) if sync else None,
@@ -327,7 +346,7 @@ def wsm_iterate_batch(h: Handle, images: list[dict], max_iter: int, eps: float,
 
 
 def wsm_map_batch(h: Handle, images: list[dict], stream=None):
-    arr = _items(images, True, False)
+    arr = _items(images, True, False, h.wide)
     _check(lib().wsm_map_batch(h.ptr, C.cast(arr, C.c_void_p), len(images), _stream(stream)))
 
 
@@ -361,7 +380,7 @@ def wsm_init_batch(h: Handle, images: list[dict], seeds: list[int], stream=None)
         it.n_unique = nu
         it.d_colors = _dev(im["colors"], torch.uint32, "colors", nu)
         it.d_centers = _dev(im["centers"], torch.float32, "centers", 4 * K)
-        it.d_labels = _dev(im["labels"], torch.uint8, "labels", nu)
+        it.d_labels = _lab(im["labels"], h.wide, "labels", nu)
     if len(seeds) != len(images):
         raise ValueError("one seed per image")
     sd = (C.c_uint64 * max(len(images), 1))(*[int(x) & (2**64 - 1) for x in seeds])
@@ -383,7 +402,7 @@ def wsm_distortion_batch(h: Handle, images: list[dict], d_mse: torch.Tensor | No
         it.pixel_stride = stride
         it.K = K
         it.d_centers = _dev(im["centers"], torch.float32, "centers", 4 * K)
-        it.d_index = _dev(im["index"], torch.uint8, "index", n)
+        it.d_index = _lab(im["index"], h.wide, "index", n)
     m = (C.c_double * max(len(images), 1))()
     _check(lib().wsm_distortion_batch(h.ptr, C.cast(arr, C.c_void_p), len(images),
                                       _dev(d_mse, torch.float64, "d_mse", len(images)),
@@ -400,7 +419,7 @@ def wsm_distortion(h: Handle, rgb: torch.Tensor, centers: torch.Tensor, K: int,
     m = C.c_double(0.0)
     _check(lib().wsm_distortion(h.ptr, _dev(rgb, torch.uint8, "rgb"), n, stride,
                                 _dev(centers, torch.float32, "centers", 4 * K), K,
-                                _dev(index, torch.uint8, "index", n),
+                                _lab(index, h.wide, "index", n),
                                 _dev(d_mse, torch.float64, "d_mse", 1),
                                 C.byref(m) if sync else None, _stream(stream)))
     return m.value if sync else None
@@ -468,7 +487,7 @@ def wsm_distortion_bwd(h: Handle, x: torch.Tensor, w: torch.Tensor | None, cente
 N_SHAPES = 5
 
 
-def pipeline_items(images: list[dict]):
+def pipeline_items(images: list[dict], wide: bool = False):
     """Marshal dicts with rgb, K, colors, counts, centers, labels, index (device
     buffers of wsm_quantize_batch) into a wsm_item array; the array keeps the
     pointers, so it can be reused for as long as the tensors live."""
@@ -485,8 +504,8 @@ def pipeline_items(images: list[dict]):
         it.d_counts = _dev(im["counts"], torch.uint32, "counts", n)
         it.n_unique = 0
         it.d_centers = _dev(im["centers"], torch.float32, "centers", 4 * K)
-        it.d_labels = _dev(im["labels"], torch.uint8, "labels", n)
-        it.d_index = _dev(im["index"], torch.uint8, "index", n)
+        it.d_labels = _lab(im["labels"], wide, "labels", n)
+        it.d_index = _lab(im["index"], wide, "index", n)
     return arr
 
 

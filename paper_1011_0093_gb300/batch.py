@@ -45,27 +45,29 @@ class BatchPlan:
         N.wsm_reserve_batch(self.handle, self.n_items)
         dev = self.device
         self.shapes = [(int(h), int(w), int(c)) for h, w, c in shapes]
+        lab = N.label_dtype(self.handle)       # uint8, or int16 for a wide handle
         self._rgb_off, rgb_total = _offsets(h * w * c for h, w, c in self.shapes)
-        self._idx_off, idx_total = _offsets(h * w for h, w, _ in self.shapes)
+        self._idx_off, idx_total = _offsets(h * w * lab.itemsize for h, w, _ in self.shapes)
         self._pal_off, pal_total = _offsets(16 * k for k in Ks)
         self.rgb_all = torch.zeros(rgb_total, dtype=torch.uint8, device=dev)
-        self.index_all = torch.zeros(idx_total, dtype=torch.uint8, device=dev)
+        self.index_all = torch.zeros(idx_total // lab.itemsize, dtype=lab, device=dev)
         self.centers_all = torch.zeros(pal_total // 4, dtype=torch.float32, device=dev)
         self.images = []
         for q, ((h, w, c), k) in enumerate(zip(self.shapes, Ks)):
             n = h * w
-            r0, i0, p0 = self._rgb_off[q], self._idx_off[q], self._pal_off[q] // 4
+            r0, p0 = self._rgb_off[q], self._pal_off[q] // 4
+            i0 = self._idx_off[q] // lab.itemsize
             self.images.append(dict(
                 rgb=self.rgb_all[r0:r0 + n * c].view(h, w, c), K=int(k),
                 colors=torch.empty(n, dtype=torch.uint32, device=dev),
                 counts=torch.empty(n, dtype=torch.uint32, device=dev),
                 centers=self.centers_all[p0:p0 + 4 * k].view(k, 4),
-                labels=torch.empty(n, dtype=torch.uint8, device=dev),
+                labels=torch.empty(n, dtype=lab, device=dev),
                 index=self.index_all[i0:i0 + n].view(h, w)))
         self.n_unique = torch.zeros(self.n_items, dtype=torch.int64, device=dev)
         self.iters = torch.zeros(self.n_items, dtype=torch.int32, device=dev)
         self.mse = torch.zeros(self.n_items, dtype=torch.float64, device=dev)
-        self._items = N.pipeline_items(self.images)
+        self._items = N.pipeline_items(self.images, self.handle.wide)
         self._seeds = N._seeds(list(seeds), self.n_items)
         self.graph = None
         self.graphs = []
@@ -109,8 +111,8 @@ class BatchPlan:
         out["mse"].copy_(self.mse, non_blocking=non_blocking)
 
     def index_offset(self, i: int) -> int:
-        """Where image i's index image starts in index_all (bytes)."""
-        return self._idx_off[i]
+        """Where image i's index image starts in index_all (elements)."""
+        return self._idx_off[i] // self.index_all.element_size()
 
     def palette_offset(self, i: int) -> int:
         """Where image i's palette starts in centers_all (floats)."""

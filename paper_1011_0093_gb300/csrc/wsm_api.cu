@@ -81,18 +81,27 @@ static std::vector<int64_t> floyd_sample(int64_t n, int K, uint64_t seed) {
 }
 
 struct InitPick {
-    uint32_t idx[WSM_MAX_K];
+    uint32_t idx[WSM_MAX_K_WIDE];
 };
 
-__global__ void k_init(const uint32_t* __restrict__ colors, int64_t n_unique, int K, InitPick pick,
-                       float4* __restrict__ centers, uint8_t* __restrict__ labels) {
-    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid < K) {
-        uint32_t c = colors[pick.idx[tid]];
-        centers[tid] = make_float4((float)((c >> 16) & 255u), (float)((c >> 8) & 255u),
-                                   (float)(c & 255u), 0.f);
+// Memberships start at 0 (uint8 or uint16: bytes of zero either way).
+__device__ __forceinline__ void zero_labels(void* labels, int64_t n, int label_bytes, int64_t t,
+                                            int64_t nt) {
+    uint8_t* p = static_cast<uint8_t*>(labels);
+    for (int64_t q = t; q < n * label_bytes; q += nt) p[q] = 0;
+}
+
+__global__ void k_init(const uint32_t* __restrict__ colors, int64_t n_unique, int K,
+                       const __grid_constant__ InitPick pick, float4* __restrict__ centers,
+                       void* __restrict__ labels, int label_bytes) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = tid; k < K; k += nt) {
+        const uint32_t c = colors[pick.idx[k]];
+        centers[k] = make_float4((float)((c >> 16) & 255u), (float)((c >> 8) & 255u),
+                                 (float)(c & 255u), 0.f);
     }
-    for (int64_t i = tid; i < n_unique; i += (int64_t)gridDim.x * blockDim.x) labels[i] = 0;
+    zero_labels(labels, n_unique, label_bytes, tid, nt);
 }
 
 // The images of one initialisation launch: image i owns the blocks
@@ -105,21 +114,23 @@ struct InitItems {
     int64_t n_unique[kMaxBatch];
     int K[kMaxBatch];
     float4* centers[kMaxBatch];
-    uint8_t* labels[kMaxBatch];
+    void* labels[kMaxBatch];
     const uint32_t* pick;
     int pick_stride;
+    int label_bytes;
 };
 
 __global__ void k_init_batch(const __grid_constant__ InitItems B) {
     const int i = item_of_block(B.first_blk, B.n_items, blockIdx.x);
     const int G = B.first_blk[i + 1] - B.first_blk[i];
     const int64_t tid = (int64_t)(blockIdx.x - B.first_blk[i]) * blockDim.x + threadIdx.x;
-    if (tid < B.K[i]) {
-        const uint32_t c = B.colors[i][B.pick[(size_t)i * B.pick_stride + tid]];
-        B.centers[i][tid] = make_float4((float)((c >> 16) & 255u), (float)((c >> 8) & 255u),
-                                        (float)(c & 255u), 0.f);
+    const int64_t nt = (int64_t)G * blockDim.x;
+    for (int64_t k = tid; k < B.K[i]; k += nt) {
+        const uint32_t c = B.colors[i][B.pick[(size_t)i * B.pick_stride + k]];
+        B.centers[i][k] = make_float4((float)((c >> 16) & 255u), (float)((c >> 8) & 255u),
+                                      (float)(c & 255u), 0.f);
     }
-    for (int64_t q = tid; q < B.n_unique[i]; q += (int64_t)G * blockDim.x) B.labels[i][q] = 0;
+    zero_labels(B.labels[i], B.n_unique[i], B.label_bytes, tid, nt);
 }
 
 // The initialisation of a batch whose N' values are on the device (written
@@ -136,15 +147,16 @@ struct InitDevItems {
     const uint32_t* colors[kMaxBatch];
     int K[kMaxBatch];
     float4* centers[kMaxBatch];
-    uint8_t* labels[kMaxBatch];
+    void* labels[kMaxBatch];
     uint64_t seed[kMaxBatch];
     unsigned* status;
+    int label_bytes;
 };
 
 __global__ void __launch_bounds__(256) k_init_dev(const __grid_constant__ InitDevItems B) {
-    __shared__ uint64_t s_draw[WSM_MAX_K];
-    __shared__ uint32_t s_pick[WSM_MAX_K];
-    __shared__ uint32_t s_sorted[WSM_MAX_K];
+    __shared__ uint64_t s_draw[WSM_MAX_K_WIDE];
+    __shared__ uint32_t s_pick[WSM_MAX_K_WIDE];
+    __shared__ uint32_t s_sorted[WSM_MAX_K_WIDE];
     const int i = blockIdx.x / kInitBlocks, j = blockIdx.x % kInitBlocks;
     const int tid = threadIdx.x;
     const int64_t n = B.n_dev[i];
@@ -157,8 +169,8 @@ __global__ void __launch_bounds__(256) k_init_dev(const __grid_constant__ InitDe
         }
         return;
     }
-    for (int64_t q = (int64_t)j * blockDim.x + tid; q < n; q += (int64_t)kInitBlocks * blockDim.x)
-        B.labels[i][q] = 0;
+    zero_labels(B.labels[i], n, B.label_bytes, (int64_t)j * blockDim.x + tid,
+                (int64_t)kInitBlocks * blockDim.x);
     if (j != 0) return;
     // Floyd step r draws t_r = draw_r mod (top_r + 1), top_r = n - K + r, and
     // takes t_r unless it is already taken, else top_r.  t_r is taken before
@@ -210,6 +222,7 @@ int init_items_dev(wsm_handle* h, const wsm_item* items, int n_items, const uint
         B.n_items = std::min(kMaxBatch, n_items - i0);
         B.n_dev = h->batch_nu + i0;
         B.status = &h->ctrl->status;
+        B.label_bytes = h->label_bytes;
         for (int q = 0; q < B.n_items; ++q) {
             const wsm_item& it = items[i0 + q];
             B.colors[q] = it.d_colors;
@@ -270,12 +283,12 @@ int alloc_slots(wsm_handle* h, int slots) {
         size_t bytes;
     } allocs[] = {
         {(void**)&h->tab, sizeof(float4) * kk * n},
-        {(void**)&h->tab_nb, kk * n},
+        {(void**)&h->tab_nb, kk * n * h->label_bytes},
         {(void**)&h->sums, sizeof(unsigned) * 2 * kCopies * 5 * (size_t)h->max_K * n},
         {(void**)&h->sums64, sizeof(unsigned long long) * 2 * kCopies * 4 * n},
         {(void**)&h->acc, sizeof(unsigned long long) * 4 * (size_t)h->max_K * n},
         {(void**)&h->trace, sizeof(double) * kMaxTrace * n},
-        {(void**)&h->lut, (size_t)kHistBins * n},
+        {(void**)&h->lut, (size_t)kHistBins * n * h->label_bytes},
         {(void**)&h->slot_ctrl, sizeof(Ctrl) * n},
         {(void**)&h->hist, sizeof(uint32_t) * kHistBins * r},
         {(void**)&h->bitmap, sizeof(uint32_t) * kMapWords * r},
@@ -284,7 +297,7 @@ int alloc_slots(wsm_handle* h, int slots) {
         {(void**)&h->batch_mse, sizeof(double) * n},
         {(void**)&h->pick, sizeof(uint32_t) * (size_t)h->max_K * n},
         {(void**)&h->plan, sizeof(int) * (n / kMaxBatch + 1) * (kMaxBatch + 1)},
-        {(void**)&h->grid, (size_t)kGridCells * n},
+        {(void**)&h->grid, (size_t)kGridCells * n * h->label_bytes},
     };
     for (auto& a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.bytes);
@@ -333,7 +346,8 @@ extern "C" const char* wsm_last_error(void) { return t_last_error.c_str(); }
 extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64_t max_unique) {
     if (!out) return fail(WSM_E_INVAL, "null output pointer");
     *out = nullptr;
-    if (max_K < 1 || max_K > WSM_MAX_K) return fail(WSM_E_INVAL, "max_K must be in [1, 256]");
+    if (max_K < 1 || max_K > WSM_MAX_K_WIDE)
+        return fail(WSM_E_INVAL, "max_K must be in [1, 1024]");
     if (max_pixels < 1 || max_pixels > WSM_MAX_PIXELS)
         return fail(WSM_E_INVAL, "max_pixels must be in [1, 2^24]");
     if (max_unique < 1 || max_unique > max_pixels)
@@ -341,6 +355,7 @@ extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64
     wsm_handle* h = new (std::nothrow) wsm_handle();
     if (!h) return fail(WSM_E_NOMEM, "host allocation failed");
     h->max_K = max_K;
+    h->label_bytes = max_K > WSM_MAX_K ? 2 : 1;
     h->max_pixels = max_pixels;
     h->max_unique = max_unique;
     cudaError_t e = cudaGetDevice(&h->device);
@@ -355,15 +370,17 @@ extern "C" int wsm_create(wsm_handle** out, int max_K, int64_t max_pixels, int64
         delete h;
         return rc;
     }
+    const int gk = std::min(max_K, WSM_MAX_K);
     struct {
         void** p;
         size_t bytes;
     } allocs[] = {
         {(void**)&h->mse_part, sizeof(double) * 1032},   // 1024 partials + result
         {(void**)&h->ctrl, sizeof(Ctrl)},
-        {(void**)&h->grad_tab, sizeof(float4) * (size_t)max_K * max_K},
-        {(void**)&h->grad_nb, (size_t)max_K * max_K},
-        {(void**)&h->grad_part, sizeof(float4) * (size_t)grad_blocks(h) * (max_K + 1)},
+        // the gradient calls take palettes of at most 256 colors
+        {(void**)&h->grad_tab, sizeof(float4) * (size_t)gk * gk},
+        {(void**)&h->grad_nb, (size_t)gk * gk},
+        {(void**)&h->grad_part, sizeof(float4) * (size_t)grad_blocks(h) * (gk + 1)},
     };
     for (auto& a : allocs) {
         e = cudaMalloc(a.p, a.bytes);
@@ -434,7 +451,7 @@ extern "C" int wsm_sync_status(wsm_handle* h, wsm_stream stream) {
 }
 
 extern "C" int wsm_init(wsm_handle* h, const uint32_t* d_colors, int64_t n_unique, int K,
-                        uint64_t seed, float* d_centers, uint8_t* d_labels, wsm_stream stream) {
+                        uint64_t seed, float* d_centers, void* d_labels, wsm_stream stream) {
     int rc = check_handle(h);
     if (rc != WSM_OK) return rc;
     if (K < 1 || K > h->max_K) return fail(WSM_E_INVAL, "K out of [1, max_K]");
@@ -448,7 +465,8 @@ extern "C" int wsm_init(wsm_handle* h, const uint32_t* d_colors, int64_t n_uniqu
     int64_t want = (n_unique + threads - 1) / threads;
     int blocks = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)h->sms * 8);
     k_init<<<blocks, threads, 0, (cudaStream_t)stream>>>(d_colors, n_unique, K, p,
-                                                          (float4*)d_centers, d_labels);
+                                                          (float4*)d_centers, d_labels,
+                                                          h->label_bytes);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_init launch");
     return WSM_OK;
@@ -491,6 +509,7 @@ extern "C" int wsm_init_batch(wsm_handle* h, const wsm_item* items, int n_items,
         B.n_items = std::min(kMaxBatch, n_items - i0);
         B.pick = h->pick + (size_t)i0 * h->max_K;
         B.pick_stride = h->max_K;
+        B.label_bytes = h->label_bytes;
         B.first_blk[0] = 0;
         for (int q = 0; q < B.n_items; ++q) {
             const wsm_item& it = items[i0 + q];

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_rows(const float* __restr
         s_thr[k] = __int_as_float(0x7f800000);
     }
     __syncthreads();
-    build_rows(K, gridDim.x, blockIdx.x, s_c, s_thr, s_wkey, tab, tab_nb);
+    build_rows<uint8_t>(K, K, gridDim.x, blockIdx.x, s_c, s_thr, s_wkey, tab, tab_nb);
 }
 
 struct GradFwd {
@@ -231,7 +231,8 @@ static int check_grad_args(wsm_handle* h, const float* d_x, int x_stride, int64_
     if (x_stride != 3 && x_stride != 4) return fail(WSM_E_INVAL, "x_stride must be 3 or 4");
     if (c_stride != 3 && c_stride != 4) return fail(WSM_E_INVAL, "c_stride must be 3 or 4");
     if (n < 0 || n > ((int64_t)1 << 31)) return fail(WSM_E_INVAL, "n must be in [0, 2^31]");
-    if (K < 1 || K > h->max_K) return fail(WSM_E_INVAL, "K out of [1, max_K]");
+    if (K < 1 || K > std::min(h->max_K, WSM_MAX_K))
+        return fail(WSM_E_INVAL, "K out of [1, min(max_K, 256)]");
     if (n > 0 && !d_x) return fail(WSM_E_INVAL, "null point pointer");
     if (!d_centers) return fail(WSM_E_INVAL, "null centers");
     return WSM_OK;

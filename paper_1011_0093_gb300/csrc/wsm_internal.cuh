@@ -66,6 +66,7 @@ struct wsm_handle {
     int device = -1;
     int sms = 0;
     int max_K = 0;
+    int label_bytes = 1;         // 1 (max_K <= 256) or 2: memberships, indices, table entries
     int64_t max_pixels = 0;
     int64_t max_unique = 0;
     int iter_shape = 0;          // index into kIterShapes used by the persistent launches
@@ -89,13 +90,13 @@ struct wsm_handle {
     // per-image scratch of the persistent kernel, one slot per image of a batch
     int slots = 0;
     float4* tab = nullptr;       // [slots][max_K^2] sorted rows: (d/4, c.x, c.y, c.z)
-    uint8_t* tab_nb = nullptr;   // [slots][max_K^2] center index of each row entry
+    uint8_t* tab_nb = nullptr;   // [slots][max_K^2] center index of each row entry (label_bytes)
     unsigned* sums = nullptr;    // [slots][2][kCopies][5 max_K] replicated sums and maxima
     unsigned long long* sums64 = nullptr;  // [slots][2][kCopies][4] SSE, distances, pixels, nonzero
     unsigned long long* acc = nullptr;     // [slots][4 max_K] S_k (3) and W_k of the last pass
     double* trace = nullptr;     // [slots][kMaxTrace]
-    uint8_t* lut = nullptr;      // [slots][2^24] color -> label
-    uint8_t* grid = nullptr;     // [slots][kGridCells] candidate center per RGB cell
+    uint8_t* lut = nullptr;      // [slots][2^24] color -> label (label_bytes each)
+    uint8_t* grid = nullptr;     // [slots][kGridCells] candidate center per RGB cell (idem)
     wsm::Ctrl* slot_ctrl = nullptr;  // [slots] barrier counter, iterations, distances
     int64_t* batch_nu = nullptr;     // [slots] N' of each image of the last wsm_reduce_batch
     double* batch_mse = nullptr;     // [slots] MSE of each image of the last wsm_distortion_batch
@@ -128,7 +129,7 @@ int init_items_dev(wsm_handle* h, const wsm_item* items, int n_items, const uint
 int iterate_items(wsm_handle* h, const wsm_item* items, int n_items, int max_iter, double eps,
                   const int64_t* n_dev, cudaStream_t s);
 int launch_sortmeans(wsm_handle* h, bool map_mode, const uint32_t* colors, const uint32_t* counts,
-                     int64_t n, int K, float* centers, uint8_t* labels, int max_iter, double eps,
+                     int64_t n, int K, float* centers, void* labels, int max_iter, double eps,
                      cudaStream_t s);
 int launch_map_items(wsm_handle* h, const wsm_item* items, int n_items, int slot0,
                      const int64_t* n_dev, bool sse, cudaStream_t s);
@@ -240,7 +241,10 @@ __device__ __forceinline__ void team_sync(int m, int ts) {
 // still leaves at least K teams over the image's G blocks (one row each),
 // counting only team sizes that give at most 8 teams per block; 1 (one warp
 // per row, several rows per warp) when even single warps are fewer than K.
-__device__ __forceinline__ int row_team_size(int K, int G, int WPB) {
+// Launches sized for palettes of more than 256 colors (KM > 256) always use
+// whole blocks: their key buffer in shared memory holds one row per block.
+__device__ __forceinline__ int row_team_size(int K, int KM, int G, int WPB) {
+    if (KM > WSM_MAX_K) return WPB;
     int ts = 1;
     for (int c = 2; c <= WPB; c *= 2)
         if (WPB / c <= 8 && (long long)G * (WPB / c) >= K) ts = c;
@@ -255,12 +259,13 @@ __device__ __forceinline__ int row_team_size(int K, int G, int WPB) {
 // matter) is its entry position.  The team's threads split the comparisons
 // of a rank when there are more of them than kept keys.  Four entries with an
 // infinite bound follow the kept ones.
-__device__ __forceinline__ void build_rows(int K, int G, int b, const float4* s_c,
+template <typename Label>
+__device__ __forceinline__ void build_rows(int K, int KM, int G, int b, const float4* s_c,
                                            const float* s_thr, unsigned long long* s_wkey,
-                                           float4* tab, uint8_t* tab_nb) {
+                                           float4* tab, Label* tab_nb) {
     __shared__ int s_len[32];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, WPB = blockDim.x >> 5;
-    const int ts = row_team_size(K, G, WPB), TT = ts * 32;
+    const int ts = row_team_size(K, KM, G, WPB), TT = ts * 32;
     const int m = wid / ts, r = threadIdx.x - m * TT;          // team, thread in team
     const int teams = G * (WPB / ts);
     unsigned long long* key = s_wkey + (size_t)m * ts * K;     // the team's buffer: ts * K
@@ -289,7 +294,7 @@ __device__ __forceinline__ void build_rows(int K, int G, int b, const float4* s_
         team_sync(m, ts);
         const int L = s_len[m];
         float4* row = tab + (size_t)p * K;
-        uint8_t* row_nb = tab_nb + (size_t)p * K;
+        Label* row_nb = tab_nb + (size_t)p * K;
         const int H = ts > 1 ? max(1, TT / L) : 1;               // threads per kept key
         if (H > 1) {
             for (int j = r; j < L; j += TT) rank_part[j] = 0;
@@ -319,7 +324,7 @@ __device__ __forceinline__ void build_rows(int K, int G, int b, const float4* s_
             const float4 ct = s_c[c];
             const float d4 = __uint_as_float((unsigned)(kj >> 32)) * 0.25f;
             row[rank] = make_float4(d4, ct.x, ct.y, ct.z);
-            row_nb[rank] = (uint8_t)c;
+            row_nb[rank] = (Label)c;
         }
         if (r < 4 && L + r < K)
             row[L + r] = make_float4(__int_as_float(0x7f800000), 0.f, 0.f, 0.f);

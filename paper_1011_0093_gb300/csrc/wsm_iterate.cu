@@ -53,7 +53,7 @@ namespace wsm {
 struct ItemDesc {
     const uint32_t* colors;    // [n] ascending 0xRRGGBB
     const uint32_t* counts;    // [n]
-    uint8_t* labels;           // [n] in/out
+    void* labels;              // [n] in/out, uint8 or uint16 (the handle's label width)
     float4* centers;           // [K] in/out (read-only in the map mode)
     int64_t n;
     int K;
@@ -63,17 +63,19 @@ struct ItemDesc {
 // Per-image scratch: slot s of each array starts at base + s * (its slot size).
 struct Scratch {
     float4* tab;               // [max_K^2] rows of (d/4, c.x, c.y, c.z), nearest first
-    uint8_t* tab_nb;           // [max_K^2] center index of each entry
+    void* tab_nb;              // [max_K^2] center index of each entry (label width)
     unsigned* sums;            // [2][kCopies][5 max_K] cluster sums (4K) and the largest
                                //   prev / min_dist of a member (K, FP32 bits), by pass parity
     unsigned long long* sums64;    // [2][kCopies][4] SSE (2^-20 units), distances, pixels,
                                    //   colors with a nonzero minimum
     unsigned long long* acc;   // [4 max_K] cluster sums of the last pass
     double* trace;             // [kMaxTrace]
-    uint8_t* lut;              // [2^24] color -> label (map mode)
-    uint8_t* grid;             // [kGridCells] a nearby center for each 16^3 cell of the RGB cube
+    void* lut;                 // [2^24] color -> label (map mode; label width)
+    void* grid;                // [kGridCells] a nearby center for each 16^3 cell of the RGB
+                               //   cube (label width)
     Ctrl* ctrl;                // barrier counter, iterations, distances
     int max_K;
+    int label_bytes;           // 1: uint8 memberships and entries; 2: uint16
 };
 
 struct BatchParams {
@@ -230,13 +232,14 @@ struct CandResult {
 // (no center past it is nearer than c_q), keeping the nearest center with
 // ties to the one latest in row p, and returns it if Algorithm 2's visit of
 // row p would meet it (d[p][t] / 4 < prev, or t = p).
+template <typename Label>
 __device__ __forceinline__ CandResult candidate_search(float x, float y, float z, int p, int q,
                                                     float prev, int K, const float4* s_c,
-                                                    const float4* tab, const uint8_t* tab_nb) {
+                                                    const float4* tab, const Label* tab_nb) {
     const float4 cq = s_c[q];
     const float dq = sq3(x, y, z, cq.x, cq.y, cq.z);
     const float4* rq = tab + (size_t)q * K;
-    const uint8_t* nq = tab_nb + (size_t)q * K;
+    const Label* nq = tab_nb + (size_t)q * K;
     int bpos = -1;                 // the best so far: c_p (-1), c_q (0) or entry bpos of row q
     float bmn = prev;
     if (dq <= prev) {              // c_q is later than c_p in row p
@@ -304,12 +307,11 @@ __device__ __forceinline__ CandResult candidate_search(float x, float y, float z
 // k_sortmeans): the warp's chunks of 32 colors, one color per lane, each
 // color's pruned visit of its row, and the per-block sums.  kCand: the first
 // pass of an iterate launch, whose search starts at the grid candidate.
-template <bool kMap, bool kCand>
+template <bool kMap, bool kCand, typename Label>
 __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K, int G, int b,
                                             int WPB, int lane, int wid, unsigned* ticket,
                                             const float4* s_c, unsigned* s_acc, const float4* tab,
-                                            const uint8_t* tab_nb, const uint8_t* grid,
-                                            uint8_t* lut,
+                                            const Label* tab_nb, const Label* grid, Label* lut,
                                             unsigned long long& sse_fx, unsigned long long& ev,
                                             unsigned long long& npix, unsigned long long& nonzero,
                                             bool& bad) {
@@ -327,11 +329,12 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
         t = __shfl_sync(0xFFFFFFFFu, t, 0);
         if (cur < n) nxt = ((int64_t)G * WPB + t) * kChunk;
     }
+    Label* const labels = static_cast<Label*>(I.labels);
     uint32_t col_n = 0, cnt_n = 0;
     int lab_n = 0;
     if (cur + lane < n) {
         col_n = __ldg(I.colors + cur + lane);
-        lab_n = I.labels[cur + lane];
+        lab_n = labels[cur + lane];
         if (!kMap || I.counts) cnt_n = __ldg(I.counts + cur + lane);
     }
     while (cur < n) {
@@ -344,7 +347,7 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
         if (nxt < n) {
             if (nxt + lane < n) {
                 col_n = __ldg(I.colors + nxt + lane);
-                lab_n = I.labels[nxt + lane];
+                lab_n = labels[nxt + lane];
                 if (!kMap || I.counts) cnt_n = __ldg(I.counts + nxt + lane);
             }
             if (lane == 0) t_after = atomicAdd(ticket, 1u);   // used after this chunk
@@ -377,7 +380,7 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
             // rounding at the bound), row p is visited as usual.
             const int q = grid[grid_cell(col)];
             if (q != p) {
-                const CandResult r = candidate_search(x, y, z, p, q, prev, K, s_c, tab, tab_nb);
+                const CandResult r = candidate_search<Label>(x, y, z, p, q, prev, K, s_c, tab, tab_nb);
                 if (r.best >= 0) {
                     scan_p = false;
                     lab = r.best;
@@ -424,9 +427,9 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
             lab = mpos ? tab_nb[(size_t)p * K + mpos] : p;
         }
         if (active) {
-            if (lab != p0) I.labels[i] = (uint8_t)lab;
+            if (lab != p0) labels[i] = (Label)lab;
             if (kMap) {
-                lut[col & 0xFFFFFFu] = (uint8_t)lab;
+                lut[col & 0xFFFFFFu] = (Label)lab;
                 // Eq. 2 over the pixels of this color, each pixel's squared
                 // distance truncated to 2^-20 units as the per-pixel MSE does
                 sse_fx += (unsigned long long)cnt * sse_fixed(1u, mn);
@@ -450,7 +453,7 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
     nonzero += nz32;
 }
 
-template <bool kMap, int kThreads>
+template <bool kMap, int kThreads, typename Label>
 __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     k_sortmeans(const __grid_constant__ BatchParams P) {
     // ---- this block's image and group
@@ -467,12 +470,12 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     if (P.n_dev && n < K) return;
     const size_t kk = (size_t)P.sc.max_K * P.sc.max_K, s5 = (size_t)5 * P.sc.max_K;
     float4* const tab = P.sc.tab + (size_t)I.slot * kk;
-    uint8_t* const tab_nb = P.sc.tab_nb + (size_t)I.slot * kk;
+    Label* const tab_nb = static_cast<Label*>(P.sc.tab_nb) + (size_t)I.slot * kk;
     unsigned* const sums = P.sc.sums + (size_t)I.slot * 2 * kCopies * s5;
     unsigned long long* const sums64 = P.sc.sums64 + (size_t)I.slot * 2 * kCopies * 4;
     unsigned long long* const acc = P.sc.acc + (size_t)I.slot * 4 * P.sc.max_K;
     double* const trace = P.sc.trace + (size_t)I.slot * kMaxTrace;
-    uint8_t* const lut = kMap ? P.sc.lut + (size_t)I.slot * kHistBins : nullptr;
+    Label* const lut = kMap ? static_cast<Label*>(P.sc.lut) + (size_t)I.slot * kHistBins : nullptr;
     Ctrl* const ctrl = P.sc.ctrl + I.slot;
 
     extern __shared__ float4 smem[];
@@ -483,7 +486,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     float4* s_cn = s_c + KM;                                                  // [KM] new centers
     unsigned* s_acc = reinterpret_cast<unsigned*>(s_cn + KM);                 // [5KM] sums, max
     float* s_thr = reinterpret_cast<float*>(s_acc + 5 * KM);                  // [KM] row bounds
-    unsigned long long* s_wkey = reinterpret_cast<unsigned long long*>(s_thr + KM);  // [WPB][KM]
+    unsigned long long* s_wkey = reinterpret_cast<unsigned long long*>(s_thr + KM);
+    // row keys: [WPB][KM], or [2 KM] for palettes of more than 256 colors
     __shared__ unsigned long long s_red[4][kThreads / 32];
     __shared__ int s_stop;
 
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     // The candidate grid (iterations only): for every 16^3 cell of the RGB
     // cube the center nearest to the cell's middle, where the first pass of
     // the launch starts each color's search (see there).
-    uint8_t* const grid = P.sc.grid + (size_t)I.slot * kGridCells;
+    Label* const grid = static_cast<Label*>(P.sc.grid) + (size_t)I.slot * kGridCells;
     const bool cand = !kMap && P.cand_start;
     if (cand) {
         for (int c = b * T + tid; c < kGridCells; c += G * T) {
@@ -514,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
                     bt = k;
                 }
             }
-            grid[c] = (uint8_t)bt;
+            grid[c] = (Label)bt;
         }
         if (!grid_sync(&ctrl->bar_count, P.status, G)) return;
     }
@@ -531,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
             const int64_t i = cur + lane;
             if (i < n) {
                 const uint32_t col = __ldg(I.colors + i);
-                int p = I.labels[i];
+                int p = static_cast<const Label*>(I.labels)[i];
                 if (p >= K) {
                     bad = true;
                     p = 0;
@@ -567,7 +571,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
             s_thr[k] = 4.f * (__uint_as_float(m) * 1.001f + 1e-3f);
         }
         __syncthreads();
-        build_rows(K, G, b, s_c, s_thr, s_wkey, tab, tab_nb);
+        build_rows<Label>(K, KM, G, b, s_c, s_thr, s_wkey, tab, tab_nb);
         if (!grid_sync(&ctrl->bar_count, P.status, G)) return;
     }
 
@@ -582,13 +586,13 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
         unsigned* const ticket = &ctrl->ticket[buf];
         if constexpr (!kMap) {
             if (cand && it == 0)
-                assign_pass<false, true>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
+                assign_pass<false, true, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
                                          tab_nb, grid, lut, sse_fx, ev, npix, nonzero, bad);
             else
-                assign_pass<false, false>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
+                assign_pass<false, false, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
                                           tab_nb, grid, lut, sse_fx, ev, npix, nonzero, bad);
         } else {
-            assign_pass<true, false>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab, tab_nb,
+            assign_pass<true, false, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab, tab_nb,
                                      grid, lut, sse_fx, ev, npix, nonzero, bad);
         }
         if (bad) atomicOr(P.status, ST_BAD_LABEL);
@@ -714,7 +718,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
         }
         __syncthreads();
         if (s_stop) break;
-        build_rows(K, G, b, s_c, s_thr, s_wkey, tab, tab_nb);
+        build_rows<Label>(K, KM, G, b, s_c, s_thr, s_wkey, tab, tab_nb);
         if (!grid_sync(&ctrl->bar_count, P.status, G)) return;
     }
 
@@ -726,19 +730,32 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
 
 // Dynamic shared memory of k_sortmeans for palettes of up to KM colors.
 static size_t sortmeans_smem(int KM, int threads) {
-    return (size_t)KM * (16 + 16 + 20 + 4) + (size_t)(threads / 32) * KM * 8;
+    const size_t keys = KM > WSM_MAX_K ? (size_t)2 * KM : (size_t)(threads / 32) * KM;
+    return (size_t)KM * (16 + 16 + 20 + 4) + keys * 8;
 }
 
 // The launch shapes of the persistent kernel: threads per block and blocks
 // per SM (the grid is that many blocks on every SM, all co-resident).
 const IterShape kIterShapes[kNumIterShapes] = {{512, 2}, {256, 4}, {1024, 1}, {256, 2}, {512, 1}};
 
-static void* sortmeans_fn(bool map_mode, int threads) {
+// The kernel for a launch; uint16 memberships only with 512 threads per
+// block (nullptr for the other shapes).
+static void* sortmeans_fn(bool map_mode, int threads, int label_bytes) {
+    if (label_bytes == 2) {
+        if (threads != 512) return nullptr;
+        return map_mode ? (void*)k_sortmeans<true, 512, uint16_t>
+                        : (void*)k_sortmeans<false, 512, uint16_t>;
+    }
     switch (threads) {
-        case 256: return map_mode ? (void*)k_sortmeans<true, 256> : (void*)k_sortmeans<false, 256>;
+        case 256:
+            return map_mode ? (void*)k_sortmeans<true, 256, uint8_t>
+                            : (void*)k_sortmeans<false, 256, uint8_t>;
         case 1024:
-            return map_mode ? (void*)k_sortmeans<true, 1024> : (void*)k_sortmeans<false, 1024>;
-        default: return map_mode ? (void*)k_sortmeans<true, 512> : (void*)k_sortmeans<false, 512>;
+            return map_mode ? (void*)k_sortmeans<true, 1024, uint8_t>
+                            : (void*)k_sortmeans<false, 1024, uint8_t>;
+        default:
+            return map_mode ? (void*)k_sortmeans<true, 512, uint8_t>
+                            : (void*)k_sortmeans<false, 512, uint8_t>;
     }
 }
 
@@ -751,7 +768,11 @@ int iterate_kernel_setup(wsm_handle* h) {
         const size_t smem = sortmeans_smem(h->max_K, sh.threads);
         int occ = 1 << 30;
         for (int m = 0; m < 2; ++m) {
-            void* fn = sortmeans_fn(m == 1, sh.threads);
+            void* fn = sortmeans_fn(m == 1, sh.threads, h->label_bytes);
+            if (!fn) {
+                occ = 0;
+                break;
+            }
             int o = 0;
             cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
@@ -786,6 +807,7 @@ static Scratch handle_scratch(wsm_handle* h) {
     sc.grid = h->grid;
     sc.ctrl = h->slot_ctrl;
     sc.max_K = h->max_K;
+    sc.label_bytes = h->label_bytes;
     return sc;
 }
 
@@ -832,15 +854,17 @@ int launch_batch(const Scratch& sc, unsigned* status, bool map_mode, const ItemD
         k_plan<<<1, 32, 0, s>>>(P, threads, grid, first_dev);
         e = cudaGetLastError();
     }
+    void* fn = sortmeans_fn(map_mode, threads, sc.label_bytes);
+    if (!fn) return fail(WSM_E_INVAL, "16-bit memberships need 512 threads per block");
     if (e == cudaSuccess)
-        e = cudaLaunchCooperativeKernel(sortmeans_fn(map_mode, threads), grid, threads, args,
-                                        sortmeans_smem(sc.max_K, threads), s);
+        e = cudaLaunchCooperativeKernel(fn, grid, threads, args, sortmeans_smem(sc.max_K, threads),
+                                        s);
     if (e != cudaSuccess) return cuda_fail(e, "sort-means launch");
     return WSM_OK;
 }
 
 int launch_sortmeans(wsm_handle* h, bool map_mode, const uint32_t* colors, const uint32_t* counts,
-                     int64_t n, int K, float* centers, uint8_t* labels, int max_iter, double eps,
+                     int64_t n, int K, float* centers, void* labels, int max_iter, double eps,
                      cudaStream_t s) {
     ItemDesc it;
     it.colors = colors;
@@ -926,7 +950,7 @@ int check_item(wsm_handle* h, const wsm_item& it, bool need_pixels, bool need_co
 using namespace wsm;
 
 extern "C" int wsm_iterate(wsm_handle* h, const uint32_t* d_colors, const uint32_t* d_counts,
-                           int64_t n_unique, int K, float* d_centers, uint8_t* d_labels,
+                           int64_t n_unique, int K, float* d_centers, void* d_labels,
                            int max_iter, double eps, int* iters_done, double* sse_trace,
                            wsm_stream stream) {
     int rc = check_handle(h);
@@ -1002,8 +1026,9 @@ extern "C" int wsm_iterate_stats(wsm_handle* h, int K, int64_t* evaluated, int64
     if (evaluated) *evaluated = (int64_t)c.evaluated;
     if (S || W) {
         if (c.iters_done < 1) return fail(WSM_E_STATE, "no completed iteration");
-        unsigned long long buf[4 * WSM_MAX_K];
-        e = cudaMemcpy(buf, h->acc, sizeof(unsigned long long) * 4 * K, cudaMemcpyDeviceToHost);
+        std::vector<unsigned long long> buf((size_t)4 * K);
+        e = cudaMemcpy(buf.data(), h->acc, sizeof(unsigned long long) * 4 * K,
+                       cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "sums copy");
         for (int k = 0; k < K; ++k) {
             if (S)
@@ -1064,12 +1089,12 @@ static int static_setup(int dev, StaticSetup** out) {
         int sms = 0, occ = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_sortmeans<false, kStaticThreads>,
+            e = cudaFuncSetAttribute(k_sortmeans<false, kStaticThreads, uint8_t>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sortmeans_smem(kStaticMaxK, kStaticThreads));
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &occ, k_sortmeans<false, kStaticThreads>, kStaticThreads,
+                &occ, k_sortmeans<false, kStaticThreads, uint8_t>, kStaticThreads,
                 sortmeans_smem(kStaticMaxK, kStaticThreads));
         if (e != cudaSuccess) return cuda_fail(e, "static set-up query");
         if (occ < 1) return fail(WSM_E_CUDA, "persistent kernel cannot be resident");
@@ -1121,6 +1146,7 @@ extern "C" int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_c
     sc.grid = base + kStaticOffGrid;
     sc.ctrl = ctrl;
     sc.max_K = kStaticMaxK;
+    sc.label_bytes = 1;
     ItemDesc it;
     it.colors = d_colors;
     it.counts = d_counts;

@@ -54,43 +54,54 @@ __device__ __forceinline__ void mse_add(MseSum& m, uint32_t key, int k, int K,
 //            (kGather) or index[p], each pixel's FP32 squared distance
 //            truncated to units of 2^-20 and added as an integer, so that the
 //            total does not depend on the order of the additions.
-// Groups of 16 pixels go with vector loads (and one 16-byte index store or
-// load) when the pixels and the index image are 16-byte aligned, then the
-// last n % 16 pixels (or all of an unaligned image) one at a time.
-template <bool kGather, bool kMse>
+// Groups of 16 pixels go with vector loads (and 16-byte index stores or
+// loads: one for uint8 labels, two for uint16) when the pixels and the index
+// image are 16-byte aligned, then the last n % 16 pixels (or all of an
+// unaligned image) one at a time.
+template <bool kGather, bool kMse, typename Label>
 __device__ __forceinline__ MseSum pixel_pass(const uint8_t* __restrict__ rgb, int64_t n,
-                                             int stride, const uint8_t* __restrict__ lut,
-                                             uint8_t* __restrict__ index, const float4* s_c,
+                                             int stride, const Label* __restrict__ lut,
+                                             Label* __restrict__ index, const float4* s_c,
                                              int K, bool skipped, int64_t t, int64_t nt) {
+    constexpr int kB = (int)sizeof(Label);              // bytes per label
+    constexpr uint32_t kMask = kB == 1 ? 0xFFu : 0xFFFFu;
     MseSum m = {0ull, false};
     if (skipped && !kGather) return m;
     int64_t done = 0;
     if (vector_ok(rgb, index)) {
         const int64_t ng = n / kGroup;
         for (int64_t g = t; g < ng; g += nt) {
-            uint32_t lab[4] = {0u, 0u, 0u, 0u};
+            uint32_t lab[4 * kB] = {};                  // the group's labels, packed
             if (!skipped) {
                 uint32_t key[kGroup];
                 pixel_keys16(rgb, g, stride, key);
                 if (kGather) {
 #pragma unroll
                     for (int j = 0; j < kGroup; ++j)
-                        lab[j >> 2] |= (uint32_t)__ldg(lut + key[j]) << (8 * (j & 3));
+                        lab[(j * kB) >> 2] |= (uint32_t)__ldg(lut + key[j]) << (8 * ((j * kB) & 3));
                 } else {
-                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(index) + g);
-                    lab[0] = v.x;
-                    lab[1] = v.y;
-                    lab[2] = v.z;
-                    lab[3] = v.w;
+#pragma unroll
+                    for (int v = 0; v < kB; ++v) {
+                        const uint4 w = __ldg(reinterpret_cast<const uint4*>(index) + g * kB + v);
+                        lab[4 * v + 0] = w.x;
+                        lab[4 * v + 1] = w.y;
+                        lab[4 * v + 2] = w.z;
+                        lab[4 * v + 3] = w.w;
+                    }
                 }
                 if (kMse) {
 #pragma unroll
                     for (int j = 0; j < kGroup; ++j)
-                        mse_add(m, key[j], (lab[j >> 2] >> (8 * (j & 3))) & 255, K, s_c);
+                        mse_add(m, key[j], (lab[(j * kB) >> 2] >> (8 * ((j * kB) & 3))) & kMask,
+                                K, s_c);
                 }
             }
-            if (kGather)
-                reinterpret_cast<uint4*>(index)[g] = make_uint4(lab[0], lab[1], lab[2], lab[3]);
+            if (kGather) {
+#pragma unroll
+                for (int v = 0; v < kB; ++v)
+                    reinterpret_cast<uint4*>(index)[g * kB + v] =
+                        make_uint4(lab[4 * v], lab[4 * v + 1], lab[4 * v + 2], lab[4 * v + 3]);
+            }
         }
         done = ng * kGroup;
     }
@@ -100,12 +111,18 @@ __device__ __forceinline__ MseSum pixel_pass(const uint8_t* __restrict__ rgb, in
             continue;
         }
         const uint32_t key = pixel_key(rgb, p, stride);
-        const int k = kGather ? __ldg(lut + key) : index[p];
-        if (kGather) index[p] = (uint8_t)k;
+        const int k = kGather ? (int)__ldg(lut + key) : (int)index[p];
+        if (kGather) index[p] = (Label)k;
         if (kMse) mse_add(m, key, k, K, s_c);
     }
     return m;
 }
+
+// Palette entries a block stages in shared memory for the MSE.
+template <typename Label>
+struct PalMax {
+    static constexpr int value = sizeof(Label) == 1 ? WSM_MAX_K : WSM_MAX_K_WIDE;
+};
 
 // The block's sum of acc over its threads (thread 0 returns it).
 __device__ __forceinline__ unsigned long long block_sum(unsigned long long acc) {
@@ -119,24 +136,26 @@ __device__ __forceinline__ unsigned long long block_sum(unsigned long long acc) 
     return t;
 }
 
+template <typename Label>
 __global__ void __launch_bounds__(kPixThreads) k_gather(const uint8_t* __restrict__ rgb,
                                                         int64_t n, int stride,
-                                                        const uint8_t* __restrict__ lut,
-                                                        uint8_t* __restrict__ index) {
-    pixel_pass<true, false>(rgb, n, stride, lut, index, nullptr, 0, false,
-                            (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                            (int64_t)gridDim.x * blockDim.x);
+                                                        const Label* __restrict__ lut,
+                                                        Label* __restrict__ index) {
+    pixel_pass<true, false, Label>(rgb, n, stride, lut, index, nullptr, 0, false,
+                                   (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                   (int64_t)gridDim.x * blockDim.x);
 }
 
 // Per-block sums of the squared errors of one image's pixels.
+template <typename Label>
 __global__ void __launch_bounds__(kPixThreads) k_mse_partial(
     const uint8_t* __restrict__ rgb, int64_t n, int stride, const float4* __restrict__ centers,
-    int K, const uint8_t* __restrict__ index, unsigned long long* __restrict__ part, Ctrl* ctrl) {
-    __shared__ float4 s_c[WSM_MAX_K];
+    int K, const Label* __restrict__ index, unsigned long long* __restrict__ part, Ctrl* ctrl) {
+    __shared__ float4 s_c[PalMax<Label>::value];
     for (int k = threadIdx.x; k < K; k += blockDim.x) s_c[k] = centers[k];
     __syncthreads();
-    const MseSum m = pixel_pass<false, true>(
-        rgb, n, stride, nullptr, const_cast<uint8_t*>(index), s_c, K, false,
+    const MseSum m = pixel_pass<false, true, Label>(
+        rgb, n, stride, nullptr, const_cast<Label*>(index), s_c, K, false,
         (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
     if (m.bad) atomicOr(&ctrl->status, ST_BAD_LABEL);
     const unsigned long long t = block_sum(m.acc);
@@ -162,11 +181,11 @@ struct PixelItems {
     int n_items;
     int first_blk[kMaxBatch + 1];
     const uint8_t* rgb[kMaxBatch];
-    uint8_t* index[kMaxBatch];
+    void* index[kMaxBatch];             // uint8 or uint16 labels (the handle's width)
     int64_t n[kMaxBatch];
     int stride[kMaxBatch];
     int K[kMaxBatch];
-    const uint8_t* lut[kMaxBatch];      // the image's color->label table (gather)
+    const void* lut[kMaxBatch];         // the image's color->label table (gather)
     const float4* centers[kMaxBatch];   // (MSE)
     double* out[kMaxBatch];             // MSE (device), always written
     double* user[kMaxBatch];            // MSE (device), a caller's copy, may be null
@@ -176,10 +195,10 @@ struct PixelItems {
                             // (index 0, MSE 0)
 };
 
-template <bool kGather, bool kMse>
+template <bool kGather, bool kMse, typename Label>
 __global__ void __launch_bounds__(kPixThreads)
     k_pixels_batch(const __grid_constant__ PixelItems B) {
-    __shared__ float4 s_c[kMse ? WSM_MAX_K : 1];
+    __shared__ float4 s_c[kMse ? PalMax<Label>::value : 1];
     const int i = item_of_block(B.first_blk, B.n_items, blockIdx.x);
     const int g = blockIdx.x - B.first_blk[i], G = B.first_blk[i + 1] - B.first_blk[i];
     const int K = B.K[i];
@@ -188,10 +207,10 @@ __global__ void __launch_bounds__(kPixThreads)
         for (int k = threadIdx.x; k < K; k += blockDim.x) s_c[k] = B.centers[i][k];
         __syncthreads();
     }
-    const MseSum m = pixel_pass<kGather, kMse>(B.rgb[i], B.n[i], B.stride[i], B.lut[i],
-                                               B.index[i], s_c, K, skipped,
-                                               (int64_t)g * blockDim.x + threadIdx.x,
-                                               (int64_t)G * blockDim.x);
+    const MseSum m = pixel_pass<kGather, kMse, Label>(
+        B.rgb[i], B.n[i], B.stride[i], static_cast<const Label*>(B.lut[i]),
+        static_cast<Label*>(B.index[i]), s_c, K, skipped, (int64_t)g * blockDim.x + threadIdx.x,
+        (int64_t)G * blockDim.x);
     if (kMse) {
         if (m.bad) atomicOr(B.status, ST_BAD_LABEL);
         const unsigned long long t = block_sum(m.acc);
@@ -253,7 +272,7 @@ int pixel_items(wsm_handle* h, const wsm_item* items, int n_items, bool gather, 
             B.n[q] = it.n_pixels;
             B.stride[q] = it.pixel_stride;
             B.K[q] = it.K;
-            B.lut[q] = h->lut + (size_t)(i0 + q) * kHistBins;
+            B.lut[q] = h->lut + (size_t)(i0 + q) * kHistBins * h->label_bytes;
             B.centers[q] = reinterpret_cast<const float4*>(it.d_centers);
             B.out[q] = h->batch_mse + i0 + q;
             B.user[q] = d_mse ? d_mse + i0 + q : nullptr;
@@ -262,10 +281,13 @@ int pixel_items(wsm_handle* h, const wsm_item* items, int n_items, bool gather, 
             B.first_blk[q + 1] = B.first_blk[q] + (int)std::min(want, share);
         }
         const int grid = B.first_blk[B.n_items];
+        const bool wide = h->label_bytes == 2;
         if (gather) {
-            k_pixels_batch<true, false><<<grid, kPixThreads, 0, s>>>(B);
+            if (wide) k_pixels_batch<true, false, uint16_t><<<grid, kPixThreads, 0, s>>>(B);
+            else k_pixels_batch<true, false, uint8_t><<<grid, kPixThreads, 0, s>>>(B);
         } else {
-            k_pixels_batch<false, true><<<grid, kPixThreads, 0, s>>>(B);
+            if (wide) k_pixels_batch<false, true, uint16_t><<<grid, kPixThreads, 0, s>>>(B);
+            else k_pixels_batch<false, true, uint8_t><<<grid, kPixThreads, 0, s>>>(B);
             k_mse_final_batch<<<B.n_items, 32, 0, s>>>(B);
         }
         cudaError_t e = cudaGetLastError();
@@ -289,13 +311,19 @@ __global__ void k_round_palette(const float4* __restrict__ centers, int K,
     }
 }
 
+// Largest palette the per-pixel calls take with this handle's labels: 256
+// for uint8 labels, 1024 for uint16.
+static int palette_limit(const wsm_handle* h) {
+    return h->label_bytes == 2 ? WSM_MAX_K_WIDE : WSM_MAX_K;
+}
+
 }  // namespace wsm
 
 using namespace wsm;
 
 extern "C" int wsm_map(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, int pixel_stride,
                        const uint32_t* d_colors, int64_t n_unique, const float* d_centers, int K,
-                       uint8_t* d_labels, uint8_t* d_index, wsm_stream stream) {
+                       void* d_labels, void* d_index, wsm_stream stream) {
     int rc = check_handle(h);
     if (rc != WSM_OK) return rc;
     if (pixel_stride != 3 && pixel_stride != 4)
@@ -316,7 +344,13 @@ extern "C" int wsm_map(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, in
     if (rc != WSM_OK) return rc;
     int64_t blocks = (n_pixels + 256 * kGroup - 1) / (256 * kGroup);
     int grid = (int)std::min<int64_t>(blocks, (int64_t)h->sms * 8);
-    k_gather<<<grid, 256, 0, s>>>(d_rgb, n_pixels, pixel_stride, h->lut, d_index);
+    if (h->label_bytes == 2)
+        k_gather<uint16_t><<<grid, 256, 0, s>>>(d_rgb, n_pixels, pixel_stride,
+                                                reinterpret_cast<const uint16_t*>(h->lut),
+                                                static_cast<uint16_t*>(d_index));
+    else
+        k_gather<uint8_t><<<grid, 256, 0, s>>>(d_rgb, n_pixels, pixel_stride, h->lut,
+                                               static_cast<uint8_t*>(d_index));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "gather launch");
     return WSM_OK;
@@ -340,7 +374,7 @@ extern "C" int wsm_map_batch(wsm_handle* h, const wsm_item* items, int n_items,
 
 extern "C" int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels,
                               int pixel_stride, const float* d_centers, int K,
-                              const uint8_t* d_index, double* d_mse, double* mse,
+                              const void* d_index, double* d_mse, double* mse,
                               wsm_stream stream) {
     int rc = check_handle(h);
     if (rc != WSM_OK) return rc;
@@ -348,7 +382,7 @@ extern "C" int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pix
         return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
     if (n_pixels < 0 || n_pixels > h->max_pixels)
         return fail(WSM_E_INVAL, "n_pixels must be in [0, max_pixels]");
-    if (K < 1 || K > WSM_MAX_K) return fail(WSM_E_INVAL, "K out of [1, 256]");
+    if (K < 1 || K > palette_limit(h)) return fail(WSM_E_INVAL, "K out of [1, palette limit]");
     if (n_pixels > 0 && (!d_rgb || !d_index)) return fail(WSM_E_INVAL, "null device pointer");
     if (!d_centers) return fail(WSM_E_INVAL, "null centers");
     if ((uintptr_t)d_centers & 15) return fail(WSM_E_INVAL, "centers must be 16-byte aligned");
@@ -359,9 +393,15 @@ extern "C" int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pix
     int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>(want, std::min(kMseMaxBlocks, 6 * h->sms)));
     unsigned long long* part = reinterpret_cast<unsigned long long*>(h->mse_part);
-    k_mse_partial<<<grid, kPixThreads, 0, s>>>(d_rgb, n_pixels, pixel_stride,
-                                                reinterpret_cast<const float4*>(d_centers), K,
-                                                d_index, part, h->ctrl);
+    const float4* c4 = reinterpret_cast<const float4*>(d_centers);
+    if (h->label_bytes == 2)
+        k_mse_partial<uint16_t><<<grid, kPixThreads, 0, s>>>(
+            d_rgb, n_pixels, pixel_stride, c4, K, static_cast<const uint16_t*>(d_index), part,
+            h->ctrl);
+    else
+        k_mse_partial<uint8_t><<<grid, kPixThreads, 0, s>>>(
+            d_rgb, n_pixels, pixel_stride, c4, K, static_cast<const uint8_t*>(d_index), part,
+            h->ctrl);
     k_mse_final<<<1, 32, 0, s>>>(part, grid, n_pixels, h->mse_part + kMseMaxBlocks, d_mse);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "distortion launch");
@@ -389,7 +429,8 @@ extern "C" int wsm_distortion_batch(wsm_handle* h, const wsm_item* items, int n_
             return fail(WSM_E_INVAL, "pixel_stride must be 3 or 4");
         if (it.n_pixels < 1 || it.n_pixels > h->max_pixels)
             return fail(WSM_E_INVAL, "n_pixels must be in [1, max_pixels]");
-        if (it.K < 1 || it.K > WSM_MAX_K) return fail(WSM_E_INVAL, "K out of [1, 256]");
+        if (it.K < 1 || it.K > palette_limit(h))
+            return fail(WSM_E_INVAL, "K out of [1, palette limit]");
         if (!it.d_rgb || !it.d_index || !it.d_centers)
             return fail(WSM_E_INVAL, "null device pointer");
         if ((uintptr_t)it.d_centers & 15)
@@ -416,7 +457,7 @@ extern "C" int wsm_round_palette(wsm_handle* h, const float* d_centers, int K, u
                                  float* d_rounded, wsm_stream stream) {
     int rc = check_handle(h);
     if (rc != WSM_OK) return rc;
-    if (K < 1 || K > WSM_MAX_K) return fail(WSM_E_INVAL, "K out of [1, 256]");
+    if (K < 1 || K > palette_limit(h)) return fail(WSM_E_INVAL, "K out of [1, palette limit]");
     if (!d_centers) return fail(WSM_E_INVAL, "null centers");
     if (((uintptr_t)d_centers & 15) || ((uintptr_t)d_rounded & 15) || ((uintptr_t)d_palette & 3))
         return fail(WSM_E_INVAL, "centers/rounded must be 16-byte, palette 4-byte aligned");

@@ -46,11 +46,11 @@ def quantize(rgb: torch.Tensor, K: int, seed: int = 0, max_iter: int = 10, eps: 
     nu = N.wsm_reduce(h, rgb, colors, counts, stream=stream)
     colors, counts = colors[:nu], counts[:nu]
     centers = torch.empty((K, 4), dtype=torch.float32, device=dev)
-    labels = torch.empty(nu, dtype=torch.uint8, device=dev)
+    labels = torch.empty(nu, dtype=N.label_dtype(h), device=dev)
     N.wsm_init(h, colors, nu, K, seed, centers, labels, stream=stream)
     iters, trace = N.wsm_iterate(h, colors, counts, nu, K, centers, labels, max_iter, eps,
                                  stream=stream)
-    index = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    index = torch.empty((H, W), dtype=N.label_dtype(h), device=dev)
     N.wsm_map(h, rgb, colors, nu, centers, K, labels, index, stream=stream)
     m = m8 = pal8 = None
     if mse:
@@ -82,8 +82,8 @@ def quantize_batch(images: list, K: int, seeds: list, max_iter: int = 10, eps: f
                           colors=torch.empty(n, dtype=torch.uint32, device=dev),
                           counts=torch.empty(n, dtype=torch.uint32, device=dev),
                           centers=torch.empty((K, 4), dtype=torch.float32, device=dev),
-                          labels=torch.empty(n, dtype=torch.uint8, device=dev),
-                          index=torch.empty((H, W), dtype=torch.uint8, device=dev)))
+                          labels=torch.empty(n, dtype=N.label_dtype(handle), device=dev),
+                          index=torch.empty((H, W), dtype=N.label_dtype(handle), device=dev)))
     N.wsm_reduce_batch(handle, items, stream=stream)
     N.wsm_init_batch(handle, items, seeds, stream=stream)
     iters = N.wsm_iterate_batch(handle, items, max_iter, eps, stream=stream)

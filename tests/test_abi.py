@@ -42,7 +42,7 @@ def test_argument_errors_without_device(libwsm):
     h = C.c_void_p()
     assert libwsm.wsm_create(C.byref(h), 0, 100, 100) == -1            # K = 0
     assert b"max_K" in libwsm.wsm_last_error()
-    assert libwsm.wsm_create(C.byref(h), 257, 100, 100) == -1          # K > 256
+    assert libwsm.wsm_create(C.byref(h), 1025, 100, 100) == -1         # K > 1024
     assert libwsm.wsm_create(C.byref(h), 16, (1 << 24) + 1, 100) == -1  # too many pixels
     assert libwsm.wsm_create(C.byref(h), 16, 100, 101) == -1           # N' > N
     assert h.value is None

@@ -210,7 +210,7 @@ def teacher_forced(wsm, h, img, K, seed, iters, paper_scan=False):
     flips = 0
     for it in range(iters):
         centers = dev(pad4(c.astype(np.float32)))
-        labels = dev(lab.astype(np.uint8))
+        labels = dev(lab.astype(np.int16 if h.wide else np.uint8))
         out = gpu_pass(wsm, h, cd, nd, len(colors), K, centers, labels)
         step, nflip = check_pass(colors, counts, c, lab, *out, it, paper_scan)
         flips += nflip
@@ -271,7 +271,7 @@ def compare_whole_path(wsm, h, img, K, seed, max_iter, eps):
     # replay: the GPU one pass at a time from its own state
     cd, nd = dev(colors), dev(counts)
     centers = torch.empty((K, 4), dtype=torch.float32, device="cuda")
-    labels = torch.empty(len(colors), dtype=torch.uint8, device="cuda")
+    labels = torch.empty(len(colors), dtype=torch.int16 if h.wide else torch.uint8, device="cuda")
     wsm.wsm_init(h, cd, len(colors), K, seed, centers, labels)
     c, lab = oracle.init(colors, K, seed)
     diverged = None
@@ -318,6 +318,53 @@ def test_whole_path_sweep512_fixed10(wsm, h, s):
     img = synth.sweep_512_one(s)
     for K in (32, 64, 128, 256):
         compare_whole_path(wsm, h, img, K, 1000 * s + K, 10, 0.0)
+
+
+# ---- palettes of more than 256 colors: 16-bit memberships ----------------------------
+
+@pytest.fixture(scope="module")
+def hw(wsm):
+    with wsm.Handle(1024, 1 << 20, 1 << 20) as handle:
+        assert handle.wide
+        yield handle
+
+
+@pytest.mark.parametrize("s,K", [(7, 512), (3, 1024)])
+def test_wide_palette_iterations_teacher_forced(wsm, hw, s, K):
+    teacher_forced(wsm, hw, synth.sweep_512_one(s), K, 300 + s, 4)
+
+
+def test_wide_palette_visits_follow_algorithm_2(wsm, hw):
+    teacher_forced(wsm, hw, synth.sweep_512_one(6), 640, 9, 2, paper_scan=True)
+
+
+@pytest.mark.parametrize("s,K", [(5, 512), (1, 300)])
+def test_wide_palette_whole_path(wsm, hw, s, K):
+    """Init, iterations, final mapping and MSE with uint16 memberships and
+    index image, against the oracle."""
+    q, ref, div = compare_whole_path(wsm, hw, synth.sweep_512_one(s), K, 77 + s, 10, 0.0)
+    assert q.index.dtype == torch.int16 and q.labels.dtype == torch.int16
+    if div is None:
+        assert int(q.index.max()) >= 256          # labels past one byte were written
+
+
+def test_wide_palette_batch_equals_single(wsm, hw):
+    """The batched graph path with a wide handle gives each image what the
+    one-image path gives it."""
+    imgs = [synth.sweep_512_one(s)[: 300 + 37 * s, : 256 + 51 * s] for s in (2, 4, 6)]
+    Ks = [300, 1024, 513]
+    seeds = [5, 6, 7]
+    plan = wsm.BatchPlan([i.shape for i in imgs], Ks, seeds, max_iter=6, handle=hw)
+    plan.load([torch.from_numpy(np.ascontiguousarray(i)) for i in imgs])
+    plan.capture()
+    plan.replay()
+    plan.sync()
+    with wsm.Handle(1024, 1 << 20, 1 << 20) as h1:
+        for q, img in enumerate(imgs):
+            one = wsm.quantize(dev(img), Ks[q], seed=seeds[q], max_iter=6, handle=h1)
+            r = plan.result(q)
+            assert torch.equal(one.centers, r["centers"]) and torch.equal(one.index, r["index"])
+            assert one.mse == r["mse"] and one.iters == r["iters"]
 
 
 # ---- mapping and distortion -------------------------------------------------------
