@@ -30,6 +30,8 @@ sweep images at K in {32, 64, 128, 256}.
 unique-color reduction, the pixel mapping and the per-pixel MSE of the
 index images, each against the measured HBM peak (the final assignment and
 the pipeline's MSE from it are timed beside them).
+``--form wide`` times the iterations at K = 256, 512 and 1024 (16-bit
+memberships above 256) on the 8 sweep images.
 ``--form grad`` times the differentiable form instead: forward + backward of
 the weighted distortion D(C, X) of a 512x512 image's pixels at K = 64, and
 200 Adam steps of palette refinement from the WSM palette.
@@ -907,6 +909,66 @@ def run_stability(args):
     h.close()
 
 
+def run_wide(args):
+    """Palettes of 256, 512 and 1024 colors on the 8 sweep images: the
+    iterations (WSM, 10) of all 8 in one persistent launch, timed with CUDA
+    events (L2 flushed before each), with 8-bit memberships at K = 256 and
+    16-bit ones (a wide handle) above; Algorithm 2's distance count as the
+    work, as in the headline roofline."""
+    import torch
+
+    import paper_1011_0093_gb300 as wsm
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    images = workload(0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    pk, _ = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    rows = []
+    for K in (256, 512, 1024):
+        h = wsm.Handle(K, H * W, H * W)
+        plan = wsm.BatchPlan([im.shape for im in images], K, list(range(8)), max_iter=ITERS,
+                             handle=h)
+        plan.load([torch.from_numpy(im) for im in images])
+        wsm.wsm_set_first_pass_start(h, False)
+        plan.run(wsm.STAGE_REDUCE | wsm.STAGE_INIT | wsm.STAGE_ITERATE)
+        evaluated, _ = plan.stats()
+        wsm.wsm_set_first_pass_start(h, True)
+        ms = []
+        for rep in range(args.warmup + args.steps):
+            plan.run(wsm.STAGE_INIT)
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.run(wsm.STAGE_ITERATE)
+            b.record(stream)
+            b.synchronize()
+            if rep >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        plan.sync()
+        t = statistics.median(ms)
+        nu = [int(v) for v in plan.n_unique.cpu()]
+        tflops = 8.0 * sum(evaluated) / (t * 1e-3) / 1e12
+        rows.append({"K": K, "labels": "uint16" if h.wide else "uint8", "iterate_ms": t,
+                     "assignments_per_s": sum(nu) * ITERS / (t * 1e-3),
+                     "algorithm2_tflops": tflops, "frac_fp32": tflops / fp32_peak})
+        h.close()
+    line = {"metric": "unique-color assignments/s per iter at K = 256, 512, 1024 (8 sweep "
+                      "images, one persistent launch)", "form": "wide",
+            "value": rows[-1]["assignments_per_s"], "unit": "assignments/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows[-1]["iterate_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "sweep 8x512x512 noise 0..24, WSM 10 iterations",
+                       "l2": "flushed before each timed launch (256 MiB write)"},
+            "by_K": rows, "fp32_peak": fp32_peak}
+    print(json.dumps(line), flush=True)
+
+
 def _hbm_image(q):
     return synth.image(4096, 4096, 12000 + q, (8 * q + 5) % 25)
 
@@ -981,7 +1043,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wsm", choices=["wsm", "reference"])
     ap.add_argument("--form", default="plain",
-                    choices=["plain", "grad", "batch", "serve", "stability", "hbm"])
+                    choices=["plain", "grad", "batch", "serve", "stability", "hbm", "wide"])
     ap.add_argument("--runs", type=int, default=100)
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--lanes", type=int, default=2)
@@ -1002,6 +1064,8 @@ def main():
         run_stability(args)
     elif args.form == "hbm":
         run_hbm(args)
+    elif args.form == "wide":
+        run_wide(args)
     else:
         run_gpu(args)
 
