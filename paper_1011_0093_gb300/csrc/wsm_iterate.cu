@@ -199,11 +199,23 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
-// The block split of a launch whose image sizes are on the device, written
-// to first_dev before the persistent kernel starts.
+// Before a launch whose image sizes are on the device: the words the
+// persistent kernel needs at zero (the slots' control blocks and both
+// parities of their accumulators, `nz` 32-bit words in three ranges) are
+// cleared by all threads, and the block split is written to first_dev by
+// thread 0 of block 0.
+struct ClearRanges {
+    unsigned* p[3];
+    size_t n[3];
+};
+
 __global__ void k_plan(const __grid_constant__ BatchParams P, int threads, int grid,
-                       int* first_dev) {
-    if (threadIdx.x != 0) return;
+                       int* first_dev, const __grid_constant__ ClearRanges Z) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nt = (size_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < 3; ++r)
+        for (size_t q = t; q < Z.n[r]; q += nt) Z.p[r][q] = 0u;
+    if (t != 0) return;
     int64_t want[kMaxBatch];
     for (int i = 0; i < P.n_items; ++i)
         want[i] = group_want(P.n_dev[P.item[i].slot], P.item[i].K, threads);
@@ -843,16 +855,23 @@ int launch_batch(const Scratch& sc, unsigned* status, bool map_mode, const ItemD
         hi = std::max(hi, items[i].slot);
     }
     const size_t nsl = (size_t)(hi - lo + 1), s5 = (size_t)5 * sc.max_K;
-    cudaError_t e = cudaMemsetAsync(sc.ctrl + lo, 0, sizeof(Ctrl) * nsl, s);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(sc.sums + (size_t)lo * 2 * kCopies * s5, 0,
-                            sizeof(unsigned) * 2 * kCopies * s5 * nsl, s);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(sc.sums64 + (size_t)lo * 2 * kCopies * 4, 0,
-                            sizeof(unsigned long long) * 2 * kCopies * 4 * nsl, s);
-    if (e == cudaSuccess && n_dev) {
-        k_plan<<<1, 32, 0, s>>>(P, threads, grid, first_dev);
+    static_assert(sizeof(Ctrl) % 4 == 0, "control blocks are cleared as 32-bit words");
+    ClearRanges Z;
+    Z.p[0] = reinterpret_cast<unsigned*>(sc.ctrl + lo);
+    Z.n[0] = sizeof(Ctrl) / 4 * nsl;
+    Z.p[1] = sc.sums + (size_t)lo * 2 * kCopies * s5;
+    Z.n[1] = 2 * kCopies * s5 * nsl;
+    Z.p[2] = reinterpret_cast<unsigned*>(sc.sums64 + (size_t)lo * 2 * kCopies * 4);
+    Z.n[2] = 2 * (2 * kCopies * 4 * nsl);
+    cudaError_t e = cudaSuccess;
+    if (n_dev) {
+        // one kernel clears and plans (fewer nodes in a captured graph)
+        k_plan<<<std::min<int>(64, (int)((Z.n[1] + 255) / 256) + 1), 256, 0, s>>>(
+            P, threads, grid, first_dev, Z);
         e = cudaGetLastError();
+    } else {
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+            e = cudaMemsetAsync(Z.p[r], 0, sizeof(unsigned) * Z.n[r], s);
     }
     void* fn = sortmeans_fn(map_mode, threads, sc.label_bytes);
     if (!fn) return fail(WSM_E_INVAL, "16-bit memberships need 512 threads per block");
