@@ -500,6 +500,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     float* s_thr = reinterpret_cast<float*>(s_acc + 5 * KM);                  // [KM] row bounds
     unsigned long long* s_wkey = reinterpret_cast<unsigned long long*>(s_thr + KM);
     // row keys: [WPB][KM], or [2 KM] for palettes of more than 256 colors
+    Label* const s_grid =                                     // [kGridCells] candidate grid
+        reinterpret_cast<Label*>(s_wkey + (KM > WSM_MAX_K ? 2 * KM : WPB * KM));
     __shared__ unsigned long long s_red[4][kThreads / 32];
     __shared__ int s_stop;
 
@@ -533,6 +535,9 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
             grid[c] = (Label)bt;
         }
         if (!grid_sync(&ctrl->bar_count, P.status, G)) return;
+        // every block keeps a copy in shared memory for the first pass
+        for (int c = tid; c < kGridCells; c += T) s_grid[c] = grid[c];
+        __syncthreads();
     }
 
     // Colors of this block: chunks of kChunk, one per lane, warp w of block b
@@ -558,7 +563,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
                 const float prev = sq3(x, y, z, cp.x, cp.y, cp.z);
                 atomicMax(s_acc + 4 * K + p, __float_as_uint(prev));
                 if (cand) {                        // the first pass also reads row q
-                    const int q = grid[grid_cell(col)];
+                    const int q = s_grid[grid_cell(col)];
                     if (q != p) {
                         const float4 cq = s_c[q];
                         const float dq = sq3(x, y, z, cq.x, cq.y, cq.z);
@@ -599,13 +604,13 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
         if constexpr (!kMap) {
             if (cand && it == 0)
                 assign_pass<false, true, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
-                                         tab_nb, grid, lut, sse_fx, ev, npix, nonzero, bad);
+                                         tab_nb, s_grid, lut, sse_fx, ev, npix, nonzero, bad);
             else
                 assign_pass<false, false, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
-                                          tab_nb, grid, lut, sse_fx, ev, npix, nonzero, bad);
+                                          tab_nb, s_grid, lut, sse_fx, ev, npix, nonzero, bad);
         } else {
             assign_pass<true, false, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab, tab_nb,
-                                     grid, lut, sse_fx, ev, npix, nonzero, bad);
+                                     s_grid, lut, sse_fx, ev, npix, nonzero, bad);
         }
         if (bad) atomicOr(P.status, ST_BAD_LABEL);
         sse_fx = warp_sum_u64(sse_fx);
@@ -741,9 +746,11 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
 #undef WSM_VISIT
 
 // Dynamic shared memory of k_sortmeans for palettes of up to KM colors.
-static size_t sortmeans_smem(int KM, int threads) {
+static size_t sortmeans_smem(int KM, int threads, bool map_mode) {
     const size_t keys = KM > WSM_MAX_K ? (size_t)2 * KM : (size_t)(threads / 32) * KM;
-    return (size_t)KM * (16 + 16 + 20 + 4) + keys * 8;
+    // the candidate grid of the first pass (iterations only)
+    const size_t grid = map_mode ? 0 : (size_t)kGridCells * (KM > WSM_MAX_K ? 2 : 1);
+    return (size_t)KM * (16 + 16 + 20 + 4) + keys * 8 + grid;
 }
 
 // The launch shapes of the persistent kernel: threads per block and blocks
@@ -777,7 +784,7 @@ int iterate_kernel_setup(wsm_handle* h) {
     h->iter_shape = -1;
     for (int q = 0; q < kNumIterShapes; ++q) {
         const IterShape& sh = kIterShapes[q];
-        const size_t smem = sortmeans_smem(h->max_K, sh.threads);
+        const size_t smem = sortmeans_smem(h->max_K, sh.threads, false);   // the larger
         int occ = 1 << 30;
         for (int m = 0; m < 2; ++m) {
             void* fn = sortmeans_fn(m == 1, sh.threads, h->label_bytes);
@@ -876,7 +883,8 @@ int launch_batch(const Scratch& sc, unsigned* status, bool map_mode, const ItemD
     void* fn = sortmeans_fn(map_mode, threads, sc.label_bytes);
     if (!fn) return fail(WSM_E_INVAL, "16-bit memberships need 512 threads per block");
     if (e == cudaSuccess)
-        e = cudaLaunchCooperativeKernel(fn, grid, threads, args, sortmeans_smem(sc.max_K, threads),
+        e = cudaLaunchCooperativeKernel(fn, grid, threads, args,
+                                        sortmeans_smem(sc.max_K, threads, map_mode),
                                         s);
     if (e != cudaSuccess) return cuda_fail(e, "sort-means launch");
     return WSM_OK;
@@ -1110,11 +1118,11 @@ static int static_setup(int dev, StaticSetup** out) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_sortmeans<false, kStaticThreads, uint8_t>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sortmeans_smem(kStaticMaxK, kStaticThreads));
+                                     (int)sortmeans_smem(kStaticMaxK, kStaticThreads, false));
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &occ, k_sortmeans<false, kStaticThreads, uint8_t>, kStaticThreads,
-                sortmeans_smem(kStaticMaxK, kStaticThreads));
+                sortmeans_smem(kStaticMaxK, kStaticThreads, false));
         if (e != cudaSuccess) return cuda_fail(e, "static set-up query");
         if (occ < 1) return fail(WSM_E_CUDA, "persistent kernel cannot be resident");
         st.scratch = static_cast<unsigned char*>(p);
