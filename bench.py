@@ -278,6 +278,10 @@ def run_gpu(args):
     plan.run(wsm.STAGE_REDUCE | wsm.STAGE_INIT | wsm.STAGE_ITERATE)
     evaluated, _ = plan.stats()
     wsm.wsm_set_first_pass_start(plan.handle, True)
+    # the launch shape of the persistent kernel, picked by the library's
+    # autotuner on these images (untimed)
+    best_shape, shape_ms = plan.tune(repeats=3)
+    shape = wsm.wsm_launch_shape(plan.handle, best_shape)[1:3]
     plan.run(wsm.STAGE_REDUCE | wsm.STAGE_INIT | wsm.STAGE_ITERATE)
     executed, _ = plan.stats()
     # one step = three captured graphs replayed back to back: unique colors +
@@ -401,7 +405,9 @@ def run_gpu(args):
                        "images_per_s_e2e": len(images) * world * args.steps / (e2e_total * 1e-3),
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}",
-                       "graph_ms_median": graph_ms},
+                       "graph_ms_median": graph_ms,
+                       "launch_shape": {"threads": shape[0], "blocks_per_sm": shape[1],
+                                        "autotune_iterate_ms": shape_ms}},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "alu", "kernel": "k_sortmeans<iterate> (8 images per launch)",
