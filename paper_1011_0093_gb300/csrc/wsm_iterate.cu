@@ -13,9 +13,10 @@
 //      pass into the new centers c_k = S_k / W_k (correctly rounded to FP32;
 //      an empty cluster keeps its center), measures that pass's SSE and
 //      applies the Sec. 3.2 stop rule (all blocks compute the same values,
-//      so all decide alike); then the warps build rows p = b, b + G, ... of
-//      the center table: row p lists, nearest first, the entries
-//      (d[p][t] / 4, c_t), ties ordered by (t != p, t), so entry 0 is p.
+//      so all decide alike); then teams of warps of the group's blocks
+//      build the rows of the center table: row p lists, nearest first, the
+//      entries (d[p][t] / 4, c_t), ties ordered by (t != p, t), so entry 0
+//      is p.
 //      A row keeps only the centers t with d[p][t] below four times a bound
 //      on the prev of any member of cluster p -- no visit of row p goes
 //      further (Sec. 2: the visit stops at d[p][t] >= 4 prev) -- followed by
@@ -392,7 +393,8 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
             // rounding at the bound), row p is visited as usual.
             const int q = grid[grid_cell(col)];
             if (q != p) {
-                const CandResult r = candidate_search<Label>(x, y, z, p, q, prev, K, s_c, tab, tab_nb);
+                const CandResult r =
+                    candidate_search<Label>(x, y, z, p, q, prev, K, s_c, tab, tab_nb);
                 if (r.best >= 0) {
                     scan_p = false;
                     lab = r.best;
@@ -603,14 +605,16 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
         unsigned* const ticket = &ctrl->ticket[buf];
         if constexpr (!kMap) {
             if (cand && it == 0)
-                assign_pass<false, true, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
-                                         tab_nb, s_grid, lut, sse_fx, ev, npix, nonzero, bad);
+                assign_pass<false, true, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc,
+                                                tab, tab_nb, s_grid, lut, sse_fx, ev, npix,
+                                                nonzero, bad);
             else
-                assign_pass<false, false, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
-                                          tab_nb, s_grid, lut, sse_fx, ev, npix, nonzero, bad);
+                assign_pass<false, false, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc,
+                                                 tab, tab_nb, s_grid, lut, sse_fx, ev, npix,
+                                                 nonzero, bad);
         } else {
-            assign_pass<true, false, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab, tab_nb,
-                                     s_grid, lut, sse_fx, ev, npix, nonzero, bad);
+            assign_pass<true, false, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
+                                            tab_nb, s_grid, lut, sse_fx, ev, npix, nonzero, bad);
         }
         if (bad) atomicOr(P.status, ST_BAD_LABEL);
         sse_fx = warp_sum_u64(sse_fx);

@@ -3,9 +3,12 @@
 //
 // Mapping: one more pruned assignment of the unique colors against the final
 // centers (the persistent sort-means kernel in map mode) scatters each
-// color's membership into a 2^24-entry uint8 color->label table; a gather
-// kernel then reads the table at every pixel's 24-bit color.  Only the N'
-// entries of this image are written, and every pixel's color is one of them.
+// color's membership into a 2^24-entry color->label table (uint8, or uint16
+// for a wide handle); a gather kernel then reads the table at every pixel's
+// 24-bit color.  Only the N' entries of this image are written, and every
+// pixel's color is one of them.  The per-pixel MSE reads the pixels and the
+// index image; the batch pipeline's MSE comes from the final assignment
+// instead (wsm_pipeline.cu).
 #include <algorithm>
 
 #include "wsm_pixels.cuh"

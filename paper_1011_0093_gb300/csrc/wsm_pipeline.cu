@@ -3,8 +3,9 @@
 //
 // wsm_quantize_batch runs unique colors (Sec. 2) -> initialisation
 // (Algorithm 2, first step) -> the Sort-Means iterations with the Sec. 3.2
-// stop rule -> final assignment and pixel mapping (Sec. 1) -> MSE (Eq. 2)
-// for every image, stream-ordered.  The number of unique colors N' of each
+// stop rule -> final assignment and pixel mapping (Sec. 1) -> MSE (Eq. 2,
+// from the final assignment's squared distances) for every image,
+// stream-ordered.  The number of unique colors N' of each
 // image stays on the device: the initialisation draws its Floyd sample from
 // it there, and the persistent launches split their blocks from it there
 // (k_plan), so the host never waits and the whole sequence can be captured
