@@ -127,7 +127,8 @@ int reduce_items(wsm_handle* h, const wsm_item* items, int n_items, cudaStream_t
 int init_items_dev(wsm_handle* h, const wsm_item* items, int n_items, const uint64_t* seeds,
                    cudaStream_t s);
 int iterate_items(wsm_handle* h, const wsm_item* items, int n_items, int max_iter, double eps,
-                  const int64_t* n_dev, cudaStream_t s);
+                  const int64_t* n_dev, cudaStream_t s, int64_t* d_n_unique = nullptr,
+                  int* d_iters = nullptr);
 int launch_sortmeans(wsm_handle* h, bool map_mode, const uint32_t* colors, const uint32_t* counts,
                      int64_t n, int K, float* centers, void* labels, int max_iter, double eps,
                      cudaStream_t s);

@@ -59,6 +59,8 @@ struct ItemDesc {
     int64_t n;
     int K;
     int slot;                  // scratch slot
+    int64_t* nu_out = nullptr;     // iterations: N' and the iterations run, written by the
+    int* iters_out = nullptr;      //   group's first block at its exit (may be null)
 };
 
 // Per-image scratch: slot s of each array starts at base + s * (its slot size).
@@ -481,7 +483,17 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     const int64_t n = P.n_dev ? P.n_dev[I.slot] : I.n;
     // sizes from the device were checked by the initialisation, which flagged
     // an image with fewer unique colors than K; such an image is skipped
-    if (P.n_dev && n < K) return;
+    // the caller's copies of N' and of the iterations run, at every exit
+    const auto outputs = [&](int iters) {
+        if (!kMap && b == 0 && threadIdx.x == 0) {
+            if (I.nu_out) *I.nu_out = n;
+            if (I.iters_out) *I.iters_out = iters;
+        }
+    };
+    if (P.n_dev && n < K) {
+        outputs(0);
+        return;
+    }
     const size_t kk = (size_t)P.sc.max_K * P.sc.max_K, s5 = (size_t)5 * P.sc.max_K;
     float4* const tab = P.sc.tab + (size_t)I.slot * kk;
     Label* const tab_nb = static_cast<Label*>(P.sc.tab_nb) + (size_t)I.slot * kk;
@@ -508,7 +520,10 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     __shared__ int s_stop;
 
     const int copy = b % kCopies;
-    if (!kMap && P.max_iter <= 0) return;
+    if (!kMap && P.max_iter <= 0) {
+        outputs(0);
+        return;
+    }
 
     // the slot's accumulators (both parities) were cleared before the launch
     for (int k = tid; k < K; k += T) s_c[k] = I.centers[k];
@@ -746,6 +761,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     // centers after the last update
     if (!kMap && b == 0)
         for (int k = tid; k < K; k += T) I.centers[k] = s_c[k];
+    outputs(ctrl->iters_done);          // written by this thread in phase A
 }
 #undef WSM_VISIT
 
@@ -933,7 +949,7 @@ int launch_map_items(wsm_handle* h, const wsm_item* items, int n_items, int slot
 // The iterations of n_items images (item i in slot i), one persistent launch
 // per kMaxBatch images; with n_dev the sizes are read on the device.
 int iterate_items(wsm_handle* h, const wsm_item* items, int n_items, int max_iter, double eps,
-                  const int64_t* n_dev, cudaStream_t s) {
+                  const int64_t* n_dev, cudaStream_t s, int64_t* d_n_unique, int* d_iters) {
     for (int i0 = 0; i0 < n_items; i0 += kMaxBatch) {
         const int m = std::min(kMaxBatch, n_items - i0);
         ItemDesc d[kMaxBatch];
@@ -946,6 +962,8 @@ int iterate_items(wsm_handle* h, const wsm_item* items, int n_items, int max_ite
             d[q].n = n_dev ? it.n_pixels : it.n_unique;   // an upper bound in device mode
             d[q].K = it.K;
             d[q].slot = i0 + q;
+            d[q].nu_out = d_n_unique ? d_n_unique + i0 + q : nullptr;
+            d[q].iters_out = d_iters ? d_iters + i0 + q : nullptr;
         }
         int rc = launch_batch(handle_scratch(h), &h->ctrl->status, false, d, m, max_iter, eps,
                               kIterShapes[h->iter_shape].threads, iter_grid(h), n_dev,

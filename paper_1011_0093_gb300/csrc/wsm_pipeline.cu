@@ -22,15 +22,6 @@
 
 namespace wsm {
 
-__global__ void k_outputs(int n_items, const int64_t* __restrict__ nu,
-                          const Ctrl* __restrict__ ctrl, int64_t* __restrict__ d_n_unique,
-                          int* __restrict__ d_iters) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_items; i += gridDim.x * blockDim.x) {
-        if (d_n_unique) d_n_unique[i] = nu[i];
-        if (d_iters) d_iters[i] = ctrl[i].iters_done;
-    }
-}
-
 // Eq. 2 of image i from its final assignment: MSE = map_sse * 2^-20 / n.
 // The assignment summed, over the unique colors, count * (squared distance
 // to the assigned center truncated to 2^-20 units), with the distances the
@@ -145,14 +136,9 @@ extern "C" int wsm_quantize_batch_stages(wsm_handle* h, const wsm_item* items, i
     if (stages & WSM_STAGE_REDUCE) rc = reduce_items(h, items, n_items, s);
     if (rc == WSM_OK && (stages & WSM_STAGE_INIT)) rc = init_items_dev(h, items, n_items, seeds, s);
     if (rc == WSM_OK && (stages & WSM_STAGE_ITERATE)) {
-        rc = iterate_items(h, items, n_items, max_iter, eps, h->batch_nu, s);
-        if (rc == WSM_OK && (d_n_unique || d_iters)) {
-            // before the mapping launch resets the slots' counters
-            k_outputs<<<(n_items + 255) / 256, 256, 0, s>>>(n_items, h->batch_nu, h->slot_ctrl,
-                                                             d_n_unique, d_iters);
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) rc = cuda_fail(e, "output launch");
-        }
+        // the persistent kernel writes N' and the iterations run of every image
+        rc = iterate_items(h, items, n_items, max_iter, eps, h->batch_nu, s, d_n_unique,
+                           d_iters);
     }
     if (rc == WSM_OK && (stages & WSM_STAGE_MAP))
         rc = map_items(h, items, n_items, h->batch_nu, true, s);
