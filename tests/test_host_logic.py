@@ -1,0 +1,43 @@
+"""Host-side logic of the Python layer that runs without a GPU: buffer
+layout of BatchPlan, the label width of a handle, and argument checks that
+fire before any device pointer is used."""
+import types
+
+import pytest
+import torch
+
+from paper_1011_0093_gb300 import _native as N
+from paper_1011_0093_gb300 import batch as B
+
+
+def test_shared_buffer_parts_are_aligned_and_disjoint():
+    sizes = [786432, 1, 255, 256, 257, 0, 3 * 173 * 97]
+    offs, total = B._offsets(sizes)
+    assert offs[0] == 0 and all(o % B._ALIGN == 0 for o in offs)
+    for q in range(len(sizes) - 1):
+        assert offs[q] + sizes[q] <= offs[q + 1]            # no overlap
+        assert offs[q + 1] - offs[q] < sizes[q] + B._ALIGN  # no more padding than needed
+    assert total >= offs[-1] + sizes[-1] and total % B._ALIGN == 0
+
+
+@pytest.mark.parametrize("max_K,dtype,wide", [(1, torch.uint8, False), (256, torch.uint8, False),
+                                              (257, torch.int16, True),
+                                              (1024, torch.int16, True)])
+def test_label_width_follows_the_palette_limit(max_K, dtype, wide):
+    h = types.SimpleNamespace(max_K=max_K)
+    assert N.label_dtype(h) == dtype
+    assert (int(max_K) > N.MAX_K) == wide
+    assert N.MAX_K == 256 and N.MAX_K_WIDE == 1024
+
+
+def test_label_arrays_of_the_wrong_width_are_refused():
+    narrow = torch.zeros(8, dtype=torch.uint8)
+    wide = torch.zeros(8, dtype=torch.int16)
+    with pytest.raises(ValueError, match="int16"):
+        N._lab(narrow, True, "labels", 8)
+    with pytest.raises(ValueError, match="uint8"):
+        N._lab(wide, False, "labels", 8)
+    assert N._lab(None, True, "labels") is None
+    # the right width still has to live on the device
+    with pytest.raises(ValueError, match="CUDA"):
+        N._lab(wide, True, "labels", 8)
