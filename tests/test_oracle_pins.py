@@ -325,6 +325,28 @@ def test_map_and_mse_brute_force():
     assert math.isclose(m, exact, rel_tol=1e-13)
 
 
+def test_map_and_mse_with_indices_beyond_one_byte():
+    """Palettes of more than 256 colors: labels up to 999 reach the index image
+    unchanged, an out-of-range index is refused, and the MSE of a palette that
+    holds every pixel's own color is 0."""
+    rng = np.random.default_rng(12)
+    img = rng.integers(0, 256, (20, 30, 3), dtype=np.uint8)
+    colors, counts = oracle.unique(img)
+    assert len(colors) <= 1000
+    labels = (np.arange(len(colors)) * 7 % 1000).astype(np.int32)   # distinct: gcd(7, 1000) = 1
+    idx = oracle.map_pixels(img, colors, labels)
+    assert idx.dtype == np.int32 and idx.max() >= 256
+    lut = {int(c): int(l) for c, l in zip(colors, labels)}
+    keys = ((img[..., 0].astype(np.int64) << 16) | (img[..., 1].astype(np.int64) << 8)
+            | img[..., 2]).ravel()
+    assert all(idx[p] == lut[int(keys[p])] for p in range(len(keys)))
+    pal = np.zeros((1000, 3))
+    pal[labels] = oracle.unpack(colors)
+    assert oracle.mse(img, pal, idx) == 0.0
+    with pytest.raises(ValueError):
+        oracle.mse(img, pal[:500], idx)
+
+
 def test_mse_psnr_closed_forms():
     img = np.array([[[0, 0, 0], [10, 20, 30]]], np.uint8)
     pal = np.array([[1, 2, 2], [10, 20, 33]], np.float64)
