@@ -289,7 +289,8 @@ WSM_API int wsm_map(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels, int p
 /* Sec. 3.1, Eq. 2: MSE = (1/N) sum_p ||x_p - c_{index_p}||^2 over the three
  * channels.  Each pixel's squared distance (FP32, difference form) is
  * truncated to units of 2^-20 and summed as an integer, so the result does
- * not depend on the order of the additions (deterministic).
+ * not depend on the order of the additions (deterministic).  K may be up to
+ * 256 (1024 with a wide handle, whose d_index is uint16), whatever max_K.
  *   d_mse  device double (may be NULL); mse host double (may be NULL; if
  *          given, the call synchronises).
  * Errors: WSM_E_INVAL (sizes, K; index >= K found). */
@@ -306,8 +307,8 @@ WSM_API int wsm_distortion(wsm_handle* h, const uint8_t* d_rgb, int64_t n_pixels
  *   d_palette  device uint8 [K][4] out (R, G, B, 0), may be NULL
  *   d_rounded  device float [K][4] out (the same colors as floats, 4th 0),
  *              16-byte aligned, may be NULL
- * Asynchronous.  Errors: WSM_E_INVAL (K out of [1, 256], null or unaligned
- * pointers). */
+ * Asynchronous.  Errors: WSM_E_INVAL (K out of [1, 256], or [1, 1024] with a
+ * wide handle; null or unaligned pointers). */
 WSM_API int wsm_round_palette(wsm_handle* h, const float* d_centers, int K, uint8_t* d_palette,
                               float* d_rounded, wsm_stream stream);
 
