@@ -27,12 +27,14 @@ class Quantized:
 
 
 def quantize(rgb: torch.Tensor, K: int, seed: int = 0, max_iter: int = 10, eps: float = 0.0,
-             handle: N.Handle | None = None, mse: bool = True, stream=None) -> Quantized:
+             handle: N.Handle | None = None, mse: bool = True, palette8: bool = False,
+             stream=None) -> Quantized:
     """Quantize one uint8 [H, W, 3|4] CUDA image to K colors.
 
     eps <= 0 runs exactly max_iter iterations (WSM); eps > 0 stops on the
     relative SSE change (WSM-C, Sec. 3.2) or at max_iter.  With mse, the MSE
-    of Eq. 2 with the FP32 palette and with its 8-bit rounding.
+    of Eq. 2 with the FP32 palette; with palette8 also the 8-bit palette and
+    the MSE with it.
     """
     if not rgb.is_cuda or rgb.dtype != torch.uint8 or rgb.dim() != 3:
         raise ValueError("rgb must be a uint8 CUDA tensor of shape [H, W, 3|4]")
@@ -55,6 +57,7 @@ def quantize(rgb: torch.Tensor, K: int, seed: int = 0, max_iter: int = 10, eps: 
     m = m8 = pal8 = None
     if mse:
         m = N.wsm_distortion(h, rgb, centers, K, index, stream=stream)
+    if palette8:
         pal8, rounded = N.wsm_round_palette(h, centers, K, stream=stream)
         m8 = N.wsm_distortion(h, rgb, rounded, K, index, stream=stream)
     return Quantized(centers, index, colors, counts, labels, nu, iters, trace, m, pal8, m8)

@@ -452,7 +452,7 @@ def test_round_palette_and_the_mse_of_the_8bit_palette(wsm, h):
     assert np.all(pal8.cpu().numpy()[:, 3] == 0)
     assert np.array_equal(rounded.cpu().numpy()[:, :3], expect.astype(np.float32))
     img = synth.image(211, 160, 31, 8)
-    q = wsm.quantize(dev(img), 64, seed=5, max_iter=10, handle=h)
+    q = wsm.quantize(dev(img), 64, seed=5, max_iter=10, handle=h, palette8=True)
     pal = oracle.round_palette(q.centers.cpu().numpy().astype(np.float64))
     assert np.array_equal(q.palette8.cpu().numpy()[:, :3], pal.astype(np.uint8))
     ref = oracle.mse(img, pal, q.index.cpu().numpy())
