@@ -177,29 +177,55 @@ __global__ void __launch_bounds__(256) k_init_dev(const __grid_constant__ InitDe
     // step r exactly when an earlier draw had the same value (that value was
     // taken then, as itself or already before), or when t_r = top_q for an
     // earlier step q that took top_q.  The first test needs no order (all
-    // pairs at once); the second follows q < r, in one pass over the steps.
+    // pairs at once).  The second links step r to the one earlier step
+    // q = t_r - (n - K), so "took top" is the OR of the first test along a
+    // chain of such links: pointer jumping resolves every chain in
+    // ceil(log2 K) rounds, each OR-ing the value at the end of a pointer and
+    // doubling the pointer's reach (s_sorted holds the pointers meanwhile).
     for (int r = tid; r < K; r += blockDim.x)
         s_draw[r] = splitmix_draw(B.seed[i], (uint64_t)r) % (uint64_t)(n - K + r + 1);
     __syncthreads();
+    constexpr uint32_t kNone = 0xFFFFFFFFu;
+    const int64_t base = n - K;
     for (int r = tid; r < K; r += blockDim.x) {
         const uint64_t t = s_draw[r];
         bool seen = false;
         for (int q = 0; q < r; ++q) seen |= s_draw[q] == t;
         s_pick[r] = seen ? 1u : 0u;                  // for now: t_r equals an earlier draw
+        const int64_t q = (int64_t)t - base;
+        s_sorted[r] = (q >= 0 && q < r) ? (uint32_t)q : kNone;
     }
     __syncthreads();
-    if (tid == 0) {
-        const int64_t base = n - K;
-        for (int r = 0; r < K; ++r) {
-            const int64_t t = (int64_t)s_draw[r];
-            bool taken = s_pick[r] != 0;
-            if (!taken && t >= base && t - base < r) taken = s_pick[t - base] == 2u;
-            s_pick[r] = taken ? 2u : 3u;             // 2: took top_r, 3: took t_r
+    constexpr int kPer = WSM_MAX_K_WIDE / 256;       // steps per thread (256 threads)
+    for (int reach = 1; reach < K; reach <<= 1) {
+        uint32_t v[kPer], pp[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int r = tid + u * 256;
+            v[u] = 0u;
+            pp[u] = kNone;
+            if (r < K) {
+                v[u] = s_pick[r];
+                pp[u] = s_sorted[r];
+                if (pp[u] != kNone) {
+                    v[u] |= s_pick[pp[u]];
+                    pp[u] = s_sorted[pp[u]];
+                }
+            }
         }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int r = tid + u * 256;
+            if (r < K) {
+                s_pick[r] = v[u];
+                s_sorted[r] = pp[u];
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int r = tid; r < K; r += blockDim.x)
-        s_pick[r] = s_pick[r] == 2u ? (uint32_t)(n - K + r) : (uint32_t)s_draw[r];
+        s_pick[r] = s_pick[r] ? (uint32_t)(n - K + r) : (uint32_t)s_draw[r];
     __syncthreads();
     for (int r = tid; r < K; r += blockDim.x) {     // the picks are distinct: rank = position
         const uint32_t v = s_pick[r];
