@@ -13,7 +13,10 @@ Workload (one step): 8 seeded 512x512 RGB images (noise amplitude swept
   roofline  the persistent sort-means kernel (dominant): evaluated distances x
           8 FLOP per launch over its CUDA-event duration, against the FP32
           CUDA-core peak (SMs x 128 lanes x 2 FLOP x max SM clock);
-  cpu_baseline  the CPU oracle on a bounded sample of the same workload.
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload
+          (single thread; cpu_baseline_all_cores: one process per core).
+The persistent kernel's launch shape comes from the library's autotuner,
+run on the same images before the graphs are captured (untimed).
 
 ``--impl reference`` times the CPU oracle instead (the reference arm).
 ``--form batch`` times the batched form instead: 64 seeded images with sides
