@@ -183,6 +183,23 @@ def test_assign_finds_exhaustive_minimum_from_any_start(levels):
     assert trials == 400
 
 
+def test_assign_finds_exhaustive_minimum_with_large_palettes():
+    """The same for palettes of more than 256 colors (memberships past one
+    byte), from random starting memberships."""
+    rng = np.random.default_rng(1024)
+    for t, K in enumerate((257, 600, 1024)):
+        colors = np.unique(rng.integers(0, 1 << 24, size=3000).astype(np.uint32))
+        centers = rng.random((K, 3)) * 255.0
+        start = rng.integers(0, K, size=len(colors)).astype(np.int32)
+        lab, mind, ev = oracle.assign(colors, centers, start)
+        x = oracle.unpack(colors)
+        full = ((x[:, None, :] - centers[None, :, :]) ** 2).sum(-1)
+        assert np.all(mind == full.min(axis=1))
+        assert np.array_equal(mind, full[np.arange(len(colors)), lab])
+        assert lab.max() >= 256
+        assert len(colors) <= ev < len(colors) * K
+
+
 def test_assign_stops_early_on_separated_clusters():
     """Well separated clusters: after convergence each color computes one distance."""
     base = np.array([[10, 10, 10], [200, 10, 10], [10, 200, 10], [10, 10, 200]])
