@@ -28,6 +28,8 @@ PIN_CALLS = [
     ("weighted == batch", pins.test_weighted_equals_batch_kmeans),
     ("monotone + termination", pins.test_sse_never_increases_and_termination_rule),
     ("map + mse brute force", pins.test_map_and_mse_brute_force),
+    ("indices beyond one byte", pins.test_map_and_mse_with_indices_beyond_one_byte),
+    ("large palettes", pins.test_assign_finds_exhaustive_minimum_with_large_palettes),
     ("mse/psnr closed forms", pins.test_mse_psnr_closed_forms),
     ("gradient FD", pins.test_distortion_gradient_finite_differences),
     ("gradient at fixed point", pins.test_gradient_vanishes_at_a_lloyd_fixed_point),
@@ -65,6 +67,10 @@ MUTANTS = [
     ("gradient sign flipped", "if (dC) dC[3 * a + c] += -2.0 * w[i] * diff;",
      "if (dC) dC[3 * a + c] += 2.0 * w[i] * diff;"),
     ("mixing constant mistyped", "0xBF58476D1CE4E5B9ull", "0xBF58476D1CE4E5B8ull"),
+    ("index image truncated to one byte", "index[p] = labels[at];",
+     "index[p] = (uint8_t)labels[at];"),
+    ("palette index range check admits K", "if (k < 0 || k >= K) return -1.0;",
+     "if (k < 0 || k > K) return -1.0;"),
 ]
 
 
@@ -80,6 +86,7 @@ def test_planted_mistake_is_rejected(what, old, new, tmp_path, monkeypatch):
         for name, call in PIN_CALLS:
             try:
                 call()
-            except (AssertionError, ValueError, ZeroDivisionError, OverflowError, IndexError):
+            except (AssertionError, ValueError, ZeroDivisionError, OverflowError, IndexError,
+                    pytest.fail.Exception):   # a pytest.raises that saw no error
                 rejected.append(name)
     assert rejected, f"no pin rejects the planted mistake: {what}"

@@ -360,8 +360,11 @@ def test_map_and_mse_with_indices_beyond_one_byte():
     pal = np.zeros((1000, 3))
     pal[labels] = oracle.unpack(colors)
     assert oracle.mse(img, pal, idx) == 0.0
-    with pytest.raises(ValueError):
-        oracle.mse(img, pal[:500], idx)
+    top = int(idx.max())                       # the smallest palette that holds every index
+    assert oracle.mse(img, pal[:top + 1], idx) == 0.0
+    for short in (500, top):
+        with pytest.raises(ValueError):
+            oracle.mse(img, pal[:short], idx)
 
 
 def test_mse_psnr_closed_forms():
