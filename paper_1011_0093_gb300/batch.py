@@ -27,6 +27,21 @@ def _offsets(nbytes):
     return offs, at
 
 
+def _pack_into(buf, offsets, shapes, images):
+    """Write each image's bytes at its offset of the flat uint8 buffer `buf`,
+    after checking that there is one image per shape and each has its shape."""
+    images = list(images)
+    if len(images) != len(shapes):
+        raise ValueError(f"{len(images)} images for a plan of {len(shapes)}")
+    for q, (im, shape, off) in enumerate(zip(images, shapes, offsets)):
+        t = torch.as_tensor(im)
+        if t.dtype != torch.uint8 or tuple(t.shape) != tuple(shape):
+            raise ValueError(f"image {q}: expected uint8 {tuple(shape)}, got "
+                             f"{t.dtype} {tuple(t.shape)}")
+        buf[off:off + t.numel()].copy_(t.reshape(-1))
+    return buf
+
+
 class BatchPlan:
     """Static device buffers for images of the given (H, W, channels) shapes,
     palette sizes K and seeds; run() enqueues the path for all of them."""
@@ -79,10 +94,7 @@ class BatchPlan:
         buf = torch.zeros(self.rgb_all.numel(), dtype=torch.uint8)
         if pin:
             buf = buf.pin_memory()
-        for q, im in enumerate(images):
-            t = torch.as_tensor(im).reshape(-1)
-            buf[self._rgb_off[q]:self._rgb_off[q] + t.numel()].copy_(t)
-        return buf
+        return _pack_into(buf, self._rgb_off, self.shapes, images)
 
     def load(self, images, non_blocking: bool = True):
         """Copy new pixels into the static input buffers, on the current
@@ -91,6 +103,9 @@ class BatchPlan:
         if isinstance(images, torch.Tensor) and images.dim() == 1:
             self.rgb_all.copy_(images, non_blocking=non_blocking)
             return
+        images = list(images)
+        if len(images) != self.n_items:
+            raise ValueError(f"{len(images)} images for a plan of {self.n_items}")
         for dst, src in zip((im["rgb"] for im in self.images), images):
             dst.copy_(torch.as_tensor(src), non_blocking=non_blocking)
 

@@ -41,3 +41,22 @@ def test_label_arrays_of_the_wrong_width_are_refused():
     # the right width still has to live on the device
     with pytest.raises(ValueError, match="CUDA"):
         N._lab(wide, True, "labels", 8)
+
+
+def test_pack_places_each_image_at_its_offset_and_checks_shapes():
+    shapes = [(3, 5, 3), (2, 2, 4), (7, 1, 3)]
+    offs, total = B._offsets(h * w * c for h, w, c in shapes)
+    g = torch.Generator().manual_seed(4)
+    imgs = [torch.randint(0, 256, s, dtype=torch.uint8, generator=g) for s in shapes]
+    buf = torch.full((total,), 77, dtype=torch.uint8)
+    B._pack_into(buf, offs, shapes, [im.numpy() for im in imgs])
+    for off, im in zip(offs, imgs):
+        assert torch.equal(buf[off:off + im.numel()], im.reshape(-1))
+    # the padding between parts is left alone
+    assert int(buf[offs[0] + imgs[0].numel()]) == 77
+    with pytest.raises(ValueError, match="2 images for a plan of 3"):
+        B._pack_into(buf, offs, shapes, imgs[:2])
+    with pytest.raises(ValueError, match="image 1"):
+        B._pack_into(buf, offs, shapes, [imgs[0], imgs[0], imgs[2]])
+    with pytest.raises(ValueError, match="uint8"):
+        B._pack_into(buf, offs, shapes, [imgs[0], imgs[1].int(), imgs[2]])
