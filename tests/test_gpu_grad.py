@@ -183,7 +183,7 @@ def test_adam_refines_the_wsm_palette(wsm, problem):
         D = wsm.weighted_distortion(X, Cp, assign=assign, warm_start=step > 0)
         D.backward()
         if D0 is None:
-            D0 = float(D)
+            D0 = float(D.detach())
         opt.step()
     D_end = float(wsm.weighted_distortion(X, Cp.detach(), assign=assign, warm_start=True))
     n64 = torch.full((n,), 1.0 / n, device="cuda")
