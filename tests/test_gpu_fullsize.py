@@ -130,3 +130,15 @@ def test_uneven_batch_to_2048_as_benchmarked(wsm, workloads):
         out = gpu_pass(wsm, h, colors, counts, nu, K, centers, labels)
     check_pass(colors.cpu().numpy(), counts.cpu().numpy(), c9, l9, *out, ITERS - 1,
                paper_scan=False)
+
+
+def test_max_size_4096_image_whole_path(wsm):
+    """The largest image a handle takes (2^24 pixels), with about 2M unique
+    colors of nearly equal weight (every channel even, uniform), through the
+    same captured path."""
+    rng = np.random.default_rng(4096)
+    img = (rng.integers(0, 128, (4096, 4096, 3), dtype=np.uint8) * 2).astype(np.uint8)
+    plan = run_as_benchmarked(wsm, [img], [77])
+    got = plan.result(0)
+    assert got["n_unique"] > 2_000_000
+    check_image(img, got)
