@@ -30,6 +30,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "wsm_arena.h"
 #include "wsm_internal.cuh"
 
 namespace wsm {
@@ -39,58 +40,30 @@ static double now_s() {
         .count();
 }
 
-// First-fit allocator over one device allocation, 256-byte granules, with
-// coalescing of neighbouring free ranges.
+// One device allocation; the placement of the requests' blocks in it is
+// ArenaBook's (wsm_arena.h).
 class Arena {
   public:
     int init(size_t bytes) {
-        bytes_ = (bytes + 255) & ~(size_t)255;
-        cudaError_t e = cudaMalloc(&base_, bytes_);
+        const size_t total = ArenaBook::round_up(bytes);
+        cudaError_t e = cudaMalloc(&base_, total);
         if (e != cudaSuccess) return cuda_fail(e, "server arena");
-        free_[0] = bytes_;
+        book_.reset(total);
         return WSM_OK;
     }
     ~Arena() {
         if (base_) cudaFree(base_);
     }
-    size_t capacity() const { return bytes_; }
-    size_t used() const { return used_; }
+    size_t capacity() const { return book_.capacity(); }
+    size_t used() const { return book_.used(); }
     // offset of a block of `bytes`, or SIZE_MAX if none is free
-    size_t alloc(size_t bytes) {
-        bytes = (bytes + 255) & ~(size_t)255;
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second < bytes) continue;
-            const size_t off = it->first, left = it->second - bytes;
-            free_.erase(it);
-            if (left) free_[off + bytes] = left;
-            used_ += bytes;
-            return off;
-        }
-        return SIZE_MAX;
-    }
-    void release(size_t off, size_t bytes) {
-        bytes = (bytes + 255) & ~(size_t)255;
-        used_ -= bytes;
-        auto next = free_.lower_bound(off);
-        if (next != free_.end() && off + bytes == next->first) {
-            bytes += next->second;
-            next = free_.erase(next);
-        }
-        if (next != free_.begin()) {
-            auto prev = std::prev(next);
-            if (prev->first + prev->second == off) {
-                prev->second += bytes;
-                return;
-            }
-        }
-        free_[off] = bytes;
-    }
+    size_t alloc(size_t bytes) { return book_.alloc(bytes); }
+    void release(size_t off, size_t bytes) { book_.release(off, bytes); }
     unsigned char* at(size_t off) const { return static_cast<unsigned char*>(base_) + off; }
 
   private:
     void* base_ = nullptr;
-    size_t bytes_ = 0, used_ = 0;
-    std::map<size_t, size_t> free_;   // offset -> size
+    ArenaBook book_;
 };
 
 struct Req {
