@@ -99,11 +99,17 @@ WSM_API const char* wsm_last_error(void);
 WSM_API int wsm_create(wsm_handle** h, int max_K, int64_t max_pixels, int64_t max_unique);
 
 /* Free the handle and its scratch (synchronises the device first).
- * NULL is accepted. */
+ * NULL is accepted.  Errors: none (always WSM_OK); a handle must be freed
+ * once. */
 WSM_API int wsm_destroy(wsm_handle* h);
 
 /* Read, report and clear the handle's device status word (synchronises
- * `stream`).  Returns WSM_OK if no kernel-side failure was recorded. */
+ * `stream`).  Returns WSM_OK if no kernel-side failure was recorded.
+ * Errors: the recorded failure -- WSM_E_TIMEOUT (a grid barrier gave up),
+ * WSM_E_CAPACITY (more unique colors than the outputs hold), WSM_E_INVAL
+ * (an image with N' < K was skipped, or a membership / index >= K was
+ * found); WSM_E_INVAL (NULL handle), WSM_E_STATE (wrong device),
+ * WSM_E_CUDA (the read failed). */
 WSM_API int wsm_sync_status(wsm_handle* h, wsm_stream stream);
 
 /* Sec. 2, data sampling + sample weighting.  The unique colors of the
@@ -167,7 +173,10 @@ WSM_API int wsm_iterate(wsm_handle* h, const uint32_t* d_colors, const uint32_t*
  * evaluated = number of distances ||x_i - c_k||^2 computed, summed over all
  * colors and iterations (one per color for the previous center plus one per
  * visited center); S [K][3] and W [K] (may be NULL) = the integer sums
- * sum n_i x_i and sum n_i of the last update. */
+ * sum n_i x_i and sum n_i of the last update.
+ * evaluated may be NULL too.  Errors: WSM_E_INVAL (K out of [1, max_K]),
+ * WSM_E_STATE (S or W asked for before any completed iteration, wrong
+ * device), WSM_E_CUDA. */
 WSM_API int wsm_iterate_stats(wsm_handle* h, int K, int64_t* evaluated, int64_t* S, int64_t* W,
                       wsm_stream stream);
 
@@ -270,7 +279,9 @@ WSM_API int wsm_map_batch(wsm_handle* h, const wsm_item* items, int n_items, wsm
  *     whose executions overlap on the GPU (other streams, other host
  *     threads) race on the array and give wrong results: order them.
  *   - iters_done / sse_trace as for wsm_iterate (if either is given the call
- *     synchronises and reports device-side failures). */
+ *     synchronises and reports device-side failures).
+ * Errors: WSM_E_INVAL (limits above, NULL pointers, centers not 16-byte
+ * aligned, a label >= K found), WSM_E_TIMEOUT, WSM_E_CUDA. */
 WSM_API int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_counts,
                                 int64_t n_unique, int K, float* d_centers, uint8_t* d_labels,
                                 int max_iter, double eps, int* iters_done, double* sse_trace,
@@ -429,7 +440,9 @@ WSM_API int wsm_set_grid_limit(wsm_handle* h, int blocks);
  * their centers and labels end as one complete run leaves them.
  *   times_ms  host float [5] (may be NULL): best time of each shape, -1 if
  *             not resident
- * Returns the chosen shape (>= 0) or an error code. */
+ * Returns the chosen shape (>= 0; with n_items = 0 the current one, nothing
+ * run) or an error code: WSM_E_INVAL (repeats out of [1, 100], items as for
+ * wsm_quantize_batch), WSM_E_TIMEOUT, WSM_E_CUDA. */
 WSM_API int wsm_autotune_batch(wsm_handle* h, const wsm_item* items, int n_items,
                                const uint64_t* seeds, int max_iter, double eps, int repeats,
                                float* times_ms, wsm_stream stream);
@@ -501,9 +514,12 @@ WSM_API int wsm_server_submit(wsm_server* s, const wsm_request* r, uint64_t* id)
  * it is not done in time (it stays queued), WSM_E_INVAL for an unknown id. */
 WSM_API int wsm_server_wait(wsm_server* s, uint64_t id, double timeout_s, wsm_result* res);
 
+/* Counters of the server since its creation (a consistent snapshot).
+ * Errors: WSM_E_INVAL (NULL argument). */
 WSM_API int wsm_server_stats_get(wsm_server* s, wsm_server_stats* st);
 
-/* Completes every queued request, then frees the server. */
+/* Completes every queued request, then frees the server.  NULL is accepted.
+ * Errors: none (always WSM_OK). */
 WSM_API int wsm_server_destroy(wsm_server* s);
 
 /* The weighted distortion of Eq. 1 (the k-means objective) with the sample
