@@ -60,3 +60,14 @@ def test_pack_places_each_image_at_its_offset_and_checks_shapes():
         B._pack_into(buf, offs, shapes, [imgs[0], imgs[0], imgs[2]])
     with pytest.raises(ValueError, match="uint8"):
         B._pack_into(buf, offs, shapes, [imgs[0], imgs[1].int(), imgs[2]])
+
+
+def test_tensor_arguments_are_checked_before_any_call():
+    cpu = torch.zeros(12, dtype=torch.uint8)
+    with pytest.raises(ValueError, match="CUDA"):
+        N._dev(cpu, torch.uint8, "rgb")
+    assert N._dev(None, torch.uint8, "rgb") is None
+    with pytest.raises(ValueError, match="3 or 4 channels"):
+        N._pixels(torch.zeros(4, 4, 2, dtype=torch.uint8))
+    assert N._pixels(torch.zeros(5, 7, 4, dtype=torch.uint8)) == (35, 4)
+    assert N._pixels(torch.zeros(6, 3, dtype=torch.uint8)) == (6, 3)
