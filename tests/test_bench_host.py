@@ -1,6 +1,7 @@
 """Host logic of the benchmark that runs without a GPU: the summary of the
 clock samples taken during the timed region (median and maximum SM clock,
-the throttle reasons seen active)."""
+the throttle reasons seen active), and the reference arm (the oracle timed
+on the host cores), whose JSON line is checked against the contract."""
 import bench
 
 
@@ -31,3 +32,36 @@ def test_clock_summary_skips_unreadable_lines():
     s = bench.ClockSampler.summarize(lines)
     assert s["samples"] == 1 and s["sm_mhz"] == 2070.0 and s["reasons"] == []
     assert bench.ClockSampler.summarize([])["reasons"] == ["no samples"]
+
+
+def _reference_arm(env_extra):
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **env_extra)
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "3"], cwd=root, env=env,
+                         capture_output=True, text=True, timeout=600, check=True).stdout
+    return [json.loads(s) for s in out.splitlines() if s.startswith("{")]
+
+
+def test_reference_arm_prints_the_contract_line():
+    """The reference arm (the oracle on the host cores) prints one JSON line
+    with the keys of the GPU arm's contract."""
+    lines = _reference_arm({"RANK": "0", "WORLD_SIZE": "1"})
+    assert len(lines) == 1
+    line = lines[0]
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == bench.UNIT and line["value"] > 0 and line["warmup"] >= 3
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    assert _reference_arm({"RANK": "1", "WORLD_SIZE": "2"}) == []
