@@ -71,3 +71,30 @@ def test_tensor_arguments_are_checked_before_any_call():
         N._pixels(torch.zeros(4, 4, 2, dtype=torch.uint8))
     assert N._pixels(torch.zeros(5, 7, 4, dtype=torch.uint8)) == (35, 4)
     assert N._pixels(torch.zeros(6, 3, dtype=torch.uint8)) == (6, 3)
+
+
+def test_product_path_never_imports_the_oracle():
+    """The package and its sources name no oracle module: importing the
+    package (and loading its library) leaves the oracle unloaded."""
+    import ast
+    import os
+    import subprocess
+    import sys
+    pkg = os.path.dirname(N.__file__)
+    for f in sorted(os.listdir(pkg)):
+        if f.endswith(".py"):
+            tree = ast.parse(open(os.path.join(pkg, f)).read())
+            for node in ast.walk(tree):
+                names = ([a.name for a in node.names] if isinstance(node, ast.Import) else
+                         [node.module or ""] if isinstance(node, ast.ImportFrom) else [])
+                assert not any(n.split(".")[0] == "oracle" for n in names), f
+    for f in os.listdir(os.path.join(pkg, "csrc")):
+        assert "oracle" not in open(os.path.join(pkg, "csrc", f)).read().lower(), f
+    from paper_1011_0093_gb300 import build as B
+    B.build()
+    root = os.path.dirname(pkg)
+    code = ("import sys, paper_1011_0093_gb300 as w; w.lib(); "
+            "print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))")
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True,
+                         text=True, check=True).stdout.strip()
+    assert out == "False"
