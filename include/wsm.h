@@ -278,8 +278,15 @@ WSM_API int wsm_map_batch(wsm_handle* h, const wsm_item* items, int n_items, wsm
  *     behind; each call clears the words that must start at zero.  Calls
  *     whose executions overlap on the GPU (other streams, other host
  *     threads) race on the array and give wrong results: order them.
- *   - iters_done / sse_trace as for wsm_iterate (if either is given the call
- *     synchronises and reports device-side failures).
+ *   - iters_done / sse_trace as for wsm_iterate.  If either is given, the
+ *     call synchronises and reports device-side failures (a barrier timeout,
+ *     a label >= K).  If neither is given, the call is asynchronous and
+ *     reports none: the failure stays recorded in the array and the next
+ *     call on this device that passes iters_done or sse_trace reports it
+ *     (and clears the record).
+ *   - Handles created or destroyed before or after a call (of any palette
+ *     size) do not affect it: the kernel's shared-memory limit on a device
+ *     is only ever raised.
  * Errors: WSM_E_INVAL (limits above, NULL pointers, centers not 16-byte
  * aligned, a label >= K found), WSM_E_TIMEOUT, WSM_E_CUDA. */
 WSM_API int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_counts,

@@ -9,7 +9,7 @@
  * it.  Every function follows the paper's steps in the paper's order and
  * notation; the section, algorithm or equation it follows is named above it.
  *
- * Readings where the paper is silent (each also listed in the design notes):
+ * Readings where the paper is silent (each stated below):
  *   R1  init: the random initial centers are K distinct indices into the
  *       unique color list, drawn with Floyd's sampling algorithm (Bentley & Floyd,
  *       CACM 1987) from a counter-based splitmix64 stream (Steele et al.,

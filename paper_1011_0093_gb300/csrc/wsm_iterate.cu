@@ -43,7 +43,9 @@
 // n_i * min_dist_i truncated to that grid), so every reduction is exact and
 // the results do not depend on the grid, the grouping or the order.
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "wsm_internal.cuh"
@@ -798,6 +800,25 @@ static void* sortmeans_fn(bool map_mode, int threads, int label_bytes) {
     }
 }
 
+// The dynamic shared-memory limit of a kernel belongs to the function on the
+// current device, not to a handle: every handle and wsm_iterate_noalloc share
+// it.  It is only ever raised, to the largest size any caller on that device
+// has asked for, so that creating a handle for a small palette never takes
+// the room away from a launch sized for a larger one.
+static cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+    static std::mutex mutex;
+    static std::map<std::pair<int, const void*>, size_t> limits;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mutex);
+    size_t& cur = limits[{dev, fn}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 // Residency of each launch shape for palettes of up to max_K colors; the
 // handle starts with the first shape that fits.
 int iterate_kernel_setup(wsm_handle* h) {
@@ -813,8 +834,7 @@ int iterate_kernel_setup(wsm_handle* h) {
                 break;
             }
             int o = 0;
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
+            cudaError_t e = raise_smem_limit(fn, smem);
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, sh.threads, smem);
             if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -1112,8 +1132,11 @@ constexpr size_t kStaticOffAcc = kStaticOffSums64 + kStaticSums64Bytes;
 constexpr size_t kStaticOffTrace = kStaticOffAcc + kStaticAccBytes;
 constexpr size_t kStaticOffGrid = kStaticOffTrace + kStaticTraceBytes;
 constexpr size_t kStaticOffCtrl = kStaticOffGrid + kGridCells;
-constexpr size_t kStaticBytes = kStaticOffCtrl + 256;           // about 1.2 MiB in total
+constexpr size_t kStaticOffStatus = kStaticOffCtrl + 256;       // outside the cleared Ctrl
+constexpr size_t kStaticBytes = kStaticOffStatus + 256;         // about 1.2 MiB in total
 static_assert(kStaticOffSums % 16 == 0 && kStaticOffCtrl % 16 == 0, "scratch alignment");
+static_assert(sizeof(Ctrl) <= kStaticOffStatus - kStaticOffCtrl,
+              "the control block must fit the room kept for it");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
@@ -1138,9 +1161,8 @@ static int static_setup(int dev, StaticSetup** out) {
         int sms = 0, occ = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_sortmeans<false, kStaticThreads, uint8_t>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sortmeans_smem(kStaticMaxK, kStaticThreads, false));
+            e = raise_smem_limit((const void*)k_sortmeans<false, kStaticThreads, uint8_t>,
+                                 sortmeans_smem(kStaticMaxK, kStaticThreads, false));
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &occ, k_sortmeans<false, kStaticThreads, uint8_t>, kStaticThreads,
@@ -1181,9 +1203,10 @@ extern "C" int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_c
     unsigned char* base = st->scratch;
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(base + kStaticOffCtrl);
     double* trace = reinterpret_cast<double*>(base + kStaticOffTrace);
-    // the status word starts at zero on every call (the launch clears the rest)
-    e = cudaMemsetAsync(&ctrl->status, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return cuda_fail(e, "wsm_iterate_noalloc status clear");
+    // The status word lies outside the control block that every launch
+    // clears: a failure of a call that did not synchronise stays recorded
+    // until a later call reads it (and only then clears it).
+    unsigned* status = reinterpret_cast<unsigned*>(base + kStaticOffStatus);
     Scratch sc;
     sc.tab = reinterpret_cast<float4*>(base);
     sc.tab_nb = base + kStaticOffNb;
@@ -1204,17 +1227,24 @@ extern "C" int wsm_iterate_noalloc(const uint32_t* d_colors, const uint32_t* d_c
     it.n = n_unique;
     it.K = K;
     it.slot = 0;
-    rc = launch_batch(sc, &ctrl->status, false, &it, 1, max_iter, eps, kStaticThreads, st->grid,
+    rc = launch_batch(sc, status, false, &it, 1, max_iter, eps, kStaticThreads, st->grid,
                       nullptr, nullptr, true, s);
     if (rc != WSM_OK) return rc;
     if (iters_done || sse_trace) {
         Ctrl host;
+        unsigned st_bits = 0;
         e = cudaMemcpyAsync(&host, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&st_bits, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "wsm_iterate_noalloc result copy");
-        if (host.status & ST_TIMEOUT)
+        if (st_bits) {
+            e = cudaMemsetAsync(status, 0, sizeof(unsigned), s);
+            if (e != cudaSuccess) return cuda_fail(e, "wsm_iterate_noalloc status clear");
+        }
+        if (st_bits & ST_TIMEOUT)
             return fail(WSM_E_TIMEOUT, "a device-side grid barrier timed out");
-        if (host.status & ST_BAD_LABEL) return fail(WSM_E_INVAL, "a membership was >= K");
+        if (st_bits & ST_BAD_LABEL) return fail(WSM_E_INVAL, "a membership was >= K");
         if (iters_done) *iters_done = host.iters_done;
         if (sse_trace && host.iters_done > 0) {
             e = cudaMemcpyAsync(sse_trace, trace,
