@@ -13,6 +13,13 @@ Workload (one step): 8 seeded 512x512 RGB images (noise amplitude swept
   roofline  the persistent sort-means kernel (dominant): evaluated distances x
           8 FLOP per launch over its CUDA-event duration, against the FP32
           CUDA-core peak (SMs x 128 lanes x 2 FLOP x max SM clock);
+  roofline_hbm  the HBM-bound kernels -- unique colors (a1), index images
+          (a7), per-pixel MSE (a8) -- on 4 images of 4096x4096, each stage
+          timed alone after the timed region: algorithmic bytes (3N + 8N',
+          3N + N + N', 4N) over the mean CUDA-event time, against the
+          measured HBM copy bandwidth;
+  value_sustained  the step repeated back to back for about 2 s, with its
+          own clock record;
   cpu_baseline  the CPU oracle on a bounded sample of the same workload
           (single thread; cpu_baseline_all_cores: one process per core).
 The persistent kernel's launch shape comes from the library's autotuner,
@@ -262,11 +269,15 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 def run_gpu(args):
+    world, rank, local = dist_env()
+    # the HBM workload's images are generated while the GPU runs the step
+    hbm_pool = hbm_pending = None
+    if rank == 0 and world == 1 and not args.no_hbm:
+        hbm_pool, hbm_pending = hbm_images_async()            # spawned, before any CUDA call
     import torch
     import torch.distributed as dist
 
     import paper_1011_0093_gb300 as wsm
-    world, rank, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
@@ -377,6 +388,26 @@ def run_gpu(args):
     clk = clocks.stop()
     plan.sync()
 
+    # sustained: the same step back to back for about 2 s (L2 flushed between
+    # steps, events around each, one synchronisation at the end), with its own
+    # clock record
+    n_sus = max(args.steps, int(2000.0 / max(statistics.median(step_ms), 1e-3)))
+    sus_clocks = ClockSampler(local)
+    sus_clocks.start()
+    barrier()
+    sus_ev = []
+    for _ in range(n_sus):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(False)
+        b.record(stream)
+        sus_ev.append((a, b))
+    barrier()
+    sus_clk = sus_clocks.stop()
+    sus_ms = sum(a.elapsed_time(b) for a, b in sus_ev)
+
     # roofline of the persistent sort-means kernel, from the timed steps
     it_ms = [e[1].elapsed_time(e[2]) for e in it_events]
     graph_ms = {name: statistics.median(e[q].elapsed_time(e[q + 1]) for e in it_events)
@@ -391,6 +422,16 @@ def run_gpu(args):
     total_ms, e2e_total, all_units = combine_ranks(total_ms, sum(e2e_ms), units_step, dev)
     value = all_units * args.steps / (total_ms * 1e-3)
     e2e_value = all_units * args.steps / (e2e_total * 1e-3)
+    sus_total, _, _ = combine_ranks(sus_ms, 0.0, units_step, dev)
+    value_sustained = all_units * n_sus / (sus_total * 1e-3)
+
+    # the HBM-bound kernels (a1, a7, a8) on large images, after the timed region
+    roof_hbm = None
+    if hbm_pending is not None:
+        hbm_imgs = hbm_pending.get()
+        hbm_pool.close()
+        roof_hbm = roofline_hbm(*hbm_stages(hbm_imgs, 10, 3))
+        del hbm_imgs
 
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -432,6 +473,11 @@ def run_gpu(args):
                          "flop_per_launch_executed": 8.0 * sum(executed),
                          "timed": "the iterate graph (plan kernel with the counter clears, "
                                   "persistent launch) between CUDA events in every step"},
+            "roofline_hbm": roof_hbm,
+            "value_sustained": value_sustained,
+            "sustained": {"steps": n_sus, "ms_per_step": sus_total / n_sus, "clocks": sus_clk,
+                          "how": "the step back to back for about 2 s, L2 flushed between "
+                                 "steps, CUDA events around each step"},
             "cpu_baseline": cpu,
             "cpu_baseline_all_cores": cpu_all,
             "clocks": clk,
@@ -985,24 +1031,38 @@ def run_wide(args):
     print(json.dumps(line), flush=True)
 
 
+HBM_IMAGES = 4
+HBM_WORKLOAD = "4 images 4096x4096 (seeds 12000..12003, noise 5, 13, 21, 4), K=256"
+
+
 def _hbm_image(q):
     return synth.image(4096, 4096, 12000 + q, (8 * q + 5) % 25)
 
 
-def run_hbm(args):
-    """The HBM-bound stages on 4096x4096 images, each timed on its own (CUDA
-    events around the stage, inputs resident, L2 flushed before each)."""
+def hbm_images_async():
+    """Start generating the HBM workload's images in spawned processes (the
+    caller collects them with .get() once it needs them)."""
     import multiprocessing as mp
-    n_img = 4
-    with mp.get_context("spawn").Pool(n_img) as pool:
-        images = pool.map(_hbm_image, range(n_img))          # before any CUDA call
+    pool = mp.get_context("spawn").Pool(HBM_IMAGES)
+    return pool, pool.map_async(_hbm_image, range(HBM_IMAGES))
+
+
+def hbm_stages(images, steps: int, warmup: int):
+    """The HBM-bound stages on the given images, each timed on its own (CUDA
+    events around the stage on the launching stream, inputs resident, L2
+    flushed before each): unique colors (a1), the final assignment, the index
+    images through the color -> label table (a7), the pipeline's MSE from the
+    assignment and the per-pixel MSE of Eq. 2 (a8).  Returns per stage the
+    mean and median ms and, for a1 / a7 / a8, the algorithmic bytes (the
+    per-unit figures: 3N + 8N', 3N + N + N', 4N), GB/s from the mean and the
+    fraction of the measured HBM peak; plus N and the N' values."""
     import torch
 
     import paper_1011_0093_gb300 as wsm
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
+    n_img = len(images)
     plan = wsm.BatchPlan([im.shape for im in images], K_PALETTE, list(range(n_img)), max_iter=2)
     plan.load([torch.from_numpy(im) for im in images])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
@@ -1011,7 +1071,7 @@ def run_hbm(args):
               "mse_from_assign": wsm.STAGE_DISTORTION,
               "mse_pixels": None}                # Eq. 2 over the pixels and the index images
     times = {k: [] for k in stages}
-    for rep in range(args.warmup + args.steps):
+    for rep in range(warmup + steps):
         for name, st in stages.items():
             flush.fill_(1)
             a = torch.cuda.Event(enable_timing=True)
@@ -1023,7 +1083,7 @@ def run_hbm(args):
                 plan.run(st)
             b.record(stream)
             b.synchronize()
-            if rep >= args.warmup:
+            if rep >= warmup:
                 times[name].append(a.elapsed_time(b))
     plan.sync()
     n_unique = [int(v) for v in plan.n_unique.cpu()]
@@ -1036,16 +1096,53 @@ def run_hbm(args):
     hbm = pk.get("hbm_gbs", 6800.0)
     rows = {}
     for name in stages:
-        rows[name] = {"ms": statistics.median(times[name])}
+        mean = sum(times[name]) / len(times[name])
+        rows[name] = {"ms": statistics.median(times[name]), "ms_mean": mean}
         if name in algo:
-            gbs = algo[name] / (rows[name]["ms"] * 1e-3) / 1e9
+            gbs = algo[name] / (mean * 1e-3) / 1e9
             rows[name].update({"algorithmic_bytes": algo[name], "GB/s": gbs, "frac": gbs / hbm})
+    del plan
+    torch.cuda.empty_cache()
+    return rows, N, n_unique, hbm, pk_kind
+
+
+def roofline_hbm(rows, N, n_unique, hbm, pk_kind):
+    """The bench line's record of the HBM-bound kernels (a1, a7, a8)."""
+    names = {"reduce": ("a1 unique colors", "k_hist24 + k_scan_count + k_scan_emit", "3N + 8N'"),
+             "index": ("a7 index images", "k_pixels_batch<1,0> (gather)", "3N + N + N'"),
+             "mse_pixels": ("a8 per-pixel MSE", "k_pixels_batch<0,1> + k_mse_final_batch",
+                            "4N")}
+    out = {"workload": HBM_WORKLOAD, "pixels": N, "unique_colors": n_unique,
+           "bound": "hbm", "peak": hbm, "unit": "GB/s",
+           "peak_kind": f"{pk_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+           "timed": "each stage alone between CUDA events on the launching stream, L2 flushed "
+                    "(256 MiB write) before each, inputs resident; achieved from the mean"}
+    for key, (row, kernels, per_unit) in names.items():
+        r = rows[key]
+        out[row] = {"kernels": kernels, "algorithmic_bytes": r["algorithmic_bytes"],
+                    "bytes_per_unit": per_unit, "ms_mean": r["ms_mean"], "ms_median": r["ms"],
+                    "achieved": r["GB/s"], "frac": r["frac"]}
+    return out
+
+
+def run_hbm(args):
+    """The HBM-bound stages on 4096x4096 images, each timed on its own (CUDA
+    events around the stage, inputs resident, L2 flushed before each)."""
+    pool, pending = hbm_images_async()                     # before any CUDA call
+    images = pending.get()
+    pool.close()
+    import torch
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rows, N, n_unique, hbm, pk_kind = hbm_stages(images, args.steps, args.warmup)
+    n_img = len(images)
     line = {"metric": "HBM-bound steps on 4096x4096 images: algorithmic GB/s vs measured HBM peak",
             "form": "hbm", "value": rows["reduce"]["GB/s"], "unit": "GB/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows["reduce"]["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": f"{n_img} images 4096x4096 (noise 5..), K=256",
+            "config": {"workload": HBM_WORKLOAD, "images": n_img,
                        "pixels": N, "unique_colors": n_unique,
                        "l2": "flushed before each stage (256 MiB write)"},
             "stages": rows, "peak": hbm, "peak_kind": pk_kind}
@@ -1065,6 +1162,8 @@ def main():
     ap.add_argument("--lanes", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-hbm", action="store_true",
+                    help="skip the HBM-bound stages on 4096x4096 images in the default form")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

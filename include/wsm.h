@@ -434,6 +434,17 @@ WSM_API int wsm_set_launch_shape(wsm_handle* h, int shape);
  * Errors: WSM_E_STATE (wrong device). */
 WSM_API int wsm_set_first_pass_start(wsm_handle* h, int candidate);
 
+/* How the handle's unique-color reductions fill their histogram (Sec. 2,
+ * data sampling; both give the same colors and counts bit for bit):
+ *   0  by size (default): bucketed when a launch's images have at least 2^20
+ *      pixels on average, direct otherwise;
+ *   1  direct: one global atomic per pixel into the 2^24-bin histogram (lanes
+ *      of a warp with the same color combined);
+ *   2  bucketed: pixels grouped by the top 10 bits of their color, then each
+ *      group counted in a shared-memory histogram and flushed once.
+ * Errors: WSM_E_INVAL (path not 0, 1 or 2), WSM_E_STATE (wrong device). */
+WSM_API int wsm_set_reduce_path(wsm_handle* h, int path);
+
 /* Limits every persistent launch of the handle to `blocks` blocks (0: the
  * whole co-resident grid of its shape), so that several handles on several
  * streams can run their persistent launches side by side on one GPU.

@@ -93,6 +93,7 @@ SIGNATURES = {
     "wsm_selftest_barrier_timeout": (C.c_int, [_P, C.c_int, _P]),
     "wsm_set_grid_limit": (C.c_int, [_P, C.c_int]),
     "wsm_set_first_pass_start": (C.c_int, [_P, C.c_int]),
+    "wsm_set_reduce_path": (C.c_int, [_P, C.c_int]),
     "wsm_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(ServerConfig)]),
     "wsm_server_submit": (C.c_int, [_P, C.POINTER(Request), C.POINTER(C.c_uint64)]),
     "wsm_server_wait": (C.c_int, [_P, C.c_uint64, C.c_double, C.POINTER(Result)]),
@@ -575,3 +576,8 @@ def wsm_set_grid_limit(h: Handle, blocks: int):
 
 def wsm_set_first_pass_start(h: Handle, candidate: bool):
     _check(lib().wsm_set_first_pass_start(h.ptr, int(bool(candidate))))
+
+
+def wsm_set_reduce_path(h: Handle, path: int):
+    """0: by size (default), 1: direct histogram, 2: bucketed (include/wsm.h)."""
+    _check(lib().wsm_set_reduce_path(h.ptr, int(path)))

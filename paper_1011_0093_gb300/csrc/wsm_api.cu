@@ -269,7 +269,8 @@ int iterate_kernel_setup(wsm_handle* h);   // wsm_iterate.cu
 void free_slots(wsm_handle* h) {
     void* ptrs[] = {h->tab,   h->tab_nb, h->sums,      h->sums64,   h->acc,       h->trace,
                     h->lut,   h->slot_ctrl, h->hist,   h->bitmap,   h->blk_total, h->batch_nu,
-                    h->batch_mse, h->pick, h->plan, h->grid};
+                    h->batch_mse, h->pick, h->plan, h->grid, h->bkt_count, h->bkt_cursor,
+                    h->keys16, h->bkt_work, h->bkt_nwork};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     void* host_ptrs[] = {h->host_nu, h->host_mse, h->host_pick};
@@ -278,6 +279,11 @@ void free_slots(wsm_handle* h) {
     h->hist = nullptr;
     h->bitmap = nullptr;
     h->blk_total = nullptr;
+    h->bkt_count = nullptr;
+    h->bkt_cursor = nullptr;
+    h->keys16 = nullptr;
+    h->bkt_work = nullptr;
+    h->bkt_nwork = nullptr;
     h->batch_nu = nullptr;
     h->batch_mse = nullptr;
     h->pick = nullptr;
@@ -319,6 +325,11 @@ int alloc_slots(wsm_handle* h, int slots) {
         {(void**)&h->hist, sizeof(uint32_t) * kHistBins * r},
         {(void**)&h->bitmap, sizeof(uint32_t) * kMapWords * r},
         {(void**)&h->blk_total, sizeof(uint32_t) * kScanBlocks * r},
+        {(void**)&h->bkt_count, sizeof(uint32_t) * kBuckets * r},
+        {(void**)&h->bkt_cursor, sizeof(uint32_t) * kBuckets * r},
+        {(void**)&h->keys16, sizeof(uint16_t) * keys_stride(h) * r},
+        {(void**)&h->bkt_work, sizeof(uint4) * (size_t)bkt_max_work(h->max_pixels) * r},
+        {(void**)&h->bkt_nwork, sizeof(int) * r},
         {(void**)&h->batch_nu, sizeof(int64_t) * n},
         {(void**)&h->batch_mse, sizeof(double) * n},
         {(void**)&h->pick, sizeof(uint32_t) * (size_t)h->max_K * n},
@@ -352,6 +363,7 @@ int alloc_slots(wsm_handle* h, int slots) {
     cudaError_t e = cudaMemset(h->slot_ctrl, 0, sizeof(Ctrl) * n);
     if (e == cudaSuccess) e = cudaMemset(h->hist, 0, sizeof(uint32_t) * kHistBins * r);
     if (e == cudaSuccess) e = cudaMemset(h->bitmap, 0, sizeof(uint32_t) * kMapWords * r);
+    if (e == cudaSuccess) e = cudaMemset(h->bkt_count, 0, sizeof(uint32_t) * kBuckets * r);
     if (e == cudaSuccess)
         e = cudaMemset(h->acc, 0, sizeof(unsigned long long) * 4 * (size_t)h->max_K * n);
     if (e != cudaSuccess) {

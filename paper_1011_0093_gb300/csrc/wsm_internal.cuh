@@ -35,6 +35,16 @@ constexpr int kChunk = 32;                   // colors per warp chunk (one per l
 constexpr int kMaxBatch = 48;                // images per persistent launch
 constexpr int kReduceSlots = 16;             // images per unique-color reduction launch
 constexpr int kGridCells = 4096;             // 16^3 cells of the first pass's candidate grid
+// Bucketed unique-color reduction (large images): buckets by the top 10 bits
+// of the 24-bit key, each with a 2^14-bin histogram that fits shared memory.
+constexpr int kBktBits = 10;
+constexpr int kBuckets = 1 << kBktBits;      // buckets per image
+constexpr int kBktBins = 1 << (24 - kBktBits);   // colors per bucket (16384)
+constexpr int kBktChunk = 16384;             // keys per bucket-histogram work item
+// work items of one image: one per nonempty bucket plus one per further chunk
+__host__ __device__ constexpr int64_t bkt_max_work(int64_t max_pixels) {
+    return (max_pixels + kBktChunk - 1) / kBktChunk + kBuckets;
+}
 
 // A launch shape of the persistent sort-means kernel.
 struct IterShape {
@@ -72,6 +82,7 @@ struct wsm_handle {
     int iter_shape = 0;          // index into kIterShapes used by the persistent launches
     int grid_limit = 0;          // > 0: at most this many blocks per persistent launch
     bool cand_start = true;      // see wsm_set_first_pass_start
+    int reduce_path = 0;         // see wsm_set_reduce_path: 0 by size, 1 direct, 2 bucketed
     bool shape_ok[wsm::kNumIterShapes] = {};   // shapes whose blocks can all be resident
     // scratch (device)
     double* mse_part = nullptr;  // [1024] block partials + [1] result
@@ -87,6 +98,11 @@ struct wsm_handle {
     uint32_t* hist = nullptr;    // [rslots][2^24] zero between calls
     uint32_t* bitmap = nullptr;  // [rslots][2^19] zero between calls
     uint32_t* blk_total = nullptr;   // [rslots][kScanBlocks]
+    uint32_t* bkt_count = nullptr;   // [rslots][kBuckets] pixels per bucket, zero between calls
+    uint32_t* bkt_cursor = nullptr;  // [rslots][kBuckets] next free key position per bucket
+    uint16_t* keys16 = nullptr;      // [rslots][max_pixels] low 14 bits of the keys, by bucket
+    uint4* bkt_work = nullptr;       // [rslots][bkt_max_work] (bucket, start, length, shared)
+    int* bkt_nwork = nullptr;        // [rslots] work items of the last planned launch
     // per-image scratch of the persistent kernel, one slot per image of a batch
     int slots = 0;
     float4* tab = nullptr;       // [slots][max_K^2] sorted rows: (d/4, c.x, c.y, c.z)
@@ -109,6 +125,10 @@ struct wsm_handle {
 
 namespace wsm {
 
+// Keys of one reduction slot in the bucketed path: max_pixels rounded up to
+// a multiple of 8 (16-byte rows of uint16).
+inline size_t keys_stride(const wsm_handle* h) { return ((size_t)h->max_pixels + 7) & ~(size_t)7; }
+
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
@@ -117,6 +137,9 @@ int read_status(wsm_handle* h, cudaStream_t s);
 int alloc_slots(wsm_handle* h, int slots);
 int grad_blocks(wsm_handle* h);
 int iter_grid(const wsm_handle* h);
+// Raise (never lower) a kernel's dynamic shared-memory limit on the current
+// device; the limit is shared by every handle.
+cudaError_t raise_smem_limit(const void* fn, size_t bytes);
 
 // Stream-ordered pieces of the batch calls (no checks, no synchronisation);
 // item i of a call uses image slot i.  With n_dev, N' of item i is read on

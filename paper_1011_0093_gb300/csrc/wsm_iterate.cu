@@ -805,7 +805,7 @@ static void* sortmeans_fn(bool map_mode, int threads, int label_bytes) {
 // it.  It is only ever raised, to the largest size any caller on that device
 // has asked for, so that creating a handle for a small palette never takes
 // the room away from a launch sized for a larger one.
-static cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
     static std::mutex mutex;
     static std::map<std::pair<int, const void*>, size_t> limits;
     int dev = -1;

@@ -1,16 +1,34 @@
 // wsm_reduce.cu -- unique colors and their frequencies (Sec. 2, data
 // sampling and sample weighting).
 //
-// The paper collects the distinct colors with a chained hash table.  Here
-// every pixel adds one to its bin of a 2^24-bin uint32 histogram (one bin per
-// 24-bit color) and, when it is the first pixel of that color, sets the
-// color's bit in a 2^24-bit occupancy map.  A two-kernel prefix scan over the
+// The paper collects the distinct colors with a chained hash table.  Here the
+// counts end up in a 2^24-bin uint32 histogram (one bin per 24-bit color)
+// with a 2^24-bit occupancy map beside it.  A two-kernel prefix scan over the
 // occupancy map then writes (color, count) for every set bit, in ascending
 // color order, and clears the bins and bits it read, so the scratch is zero
 // again for the next image without a 64 MiB memset.
+//
+// Two ways fill the histogram, with identical results (every count is an
+// exact integer sum):
+//   direct    every pixel adds one to its bin with a global atomic (lanes of a
+//             warp holding the same color add together), the first pixel of a
+//             color sets its bit.  Few launches; the cost is one L2 atomic on
+//             a random bin per pixel, so it suits small images.
+//   bucketed  (large images) the pixels are first grouped by bucket, the top
+//             10 bits of their key: one pass counts the pixels of each bucket,
+//             a plan kernel turns the counts into bucket offsets and a work
+//             list, a second pass writes each pixel's low 14 bits into its
+//             bucket's run (staged in shared memory so that every run is
+//             written contiguously), and then each work item -- one bucket, or
+//             a chunk of a large one -- counts its keys in a 2^14-bin
+//             shared-memory histogram and flushes the nonzero bins into the
+//             global histogram and occupancy map (plain stores when the bucket
+//             is one item, atomics when several items share it).  Global
+//             atomics drop from one per pixel to about one per distinct color.
 #include <algorithm>
 
 #include "wsm_internal.cuh"
+#include "wsm_pixels.cuh"
 
 namespace wsm {
 
@@ -33,6 +51,14 @@ struct ReduceItems {
     uint32_t* bitmap;                // slot i at bitmap + i * 2^19
     uint32_t* blk_total;             // slot i at blk_total + i * kScanBlocks
     unsigned* status;
+    // bucketed path
+    uint32_t* bkt_count;             // slot i at bkt_count + i * kBuckets
+    uint32_t* bkt_cursor;            // slot i at bkt_cursor + i * kBuckets
+    uint16_t* keys16;                // slot i at keys16 + i * keys_stride
+    uint4* work;                     // slot i at work + i * work_stride
+    int* n_work;                     // [slot]
+    int64_t keys_stride;
+    int64_t work_stride;
 };
 
 // Histogram with warp aggregation: lanes holding the same color elect one
@@ -57,6 +83,327 @@ __global__ void __launch_bounds__(256) k_hist24(const __grid_constant__ ReduceIt
             unsigned old = atomicAdd(hist + key, (unsigned)__popc(peers));
             if (old == 0) atomicOr(bitmap + (key >> 5), 1u << (key & 31));
         }
+    }
+}
+
+// ---- bucketed path -------------------------------------------------------------
+
+// The pixels of block g (of G) of image i, 16 consecutive pixels per thread
+// and step: calls f(key) for each (the vector path for 16-byte aligned
+// images, one pixel at a time for the rest and the last n % 16 pixels).
+template <typename F>
+__device__ __forceinline__ void for_pixels(const uint8_t* __restrict__ rgb, int64_t n, int stride,
+                                           int64_t t, int64_t nt, F&& f) {
+    int64_t done = 0;
+    if (vector_ok(rgb, nullptr)) {
+        const int64_t ng = n / kGroup;
+        for (int64_t gr = t; gr < ng; gr += nt) {
+            uint32_t key[kGroup];
+            pixel_keys16(rgb, gr, stride, key);
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) f(key[j]);
+        }
+        done = ng * kGroup;
+    }
+    for (int64_t p = done + t; p < n; p += nt) f(pixel_key(rgb, p, stride));
+}
+
+// Shared-memory slot of bucket b (= R << 2 | G >> 6): R in the low bits, so
+// that the buckets of nearby colors (a noisy region spans a few dozen
+// consecutive R values) fall in different banks.
+__device__ __forceinline__ unsigned bslot(unsigned b) { return ((b & 3u) << 8) | (b >> 2); }
+
+// Pass A: the number of pixels of each bucket.  A thread adds a run of equal
+// buckets among its consecutive pixels with one shared-memory atomic; each
+// block adds its nonzero counts to the image's.
+__global__ void __launch_bounds__(256) k_bkt_count(const __grid_constant__ ReduceItems R) {
+    __shared__ unsigned s_cnt[kBuckets];
+    const int i = item_of_block(R.first_blk, R.n_items, blockIdx.x);
+    const int g = blockIdx.x - R.first_blk[i], G = R.first_blk[i + 1] - R.first_blk[i];
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) s_cnt[b] = 0u;
+    __syncthreads();
+    unsigned run_b = 0xFFFFFFFFu, run_n = 0;
+    for_pixels(R.rgb[i], R.n[i], R.stride[i], (int64_t)g * blockDim.x + threadIdx.x,
+               (int64_t)G * blockDim.x, [&](uint32_t key) {
+                   const unsigned b = key >> (24 - kBktBits);
+                   if (b != run_b) {
+                       if (run_n) atomicAdd(&s_cnt[bslot(run_b)], run_n);
+                       run_b = b;
+                       run_n = 0;
+                   }
+                   ++run_n;
+               });
+    if (run_n) atomicAdd(&s_cnt[bslot(run_b)], run_n);
+    __syncthreads();
+    uint32_t* cnt = R.bkt_count + (size_t)i * kBuckets;
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) {
+        const unsigned c = s_cnt[bslot(b)];
+        if (c) atomicAdd(cnt + b, c);
+    }
+}
+
+// Block-wide exclusive scan of one value per thread (kBuckets threads);
+// returns the thread's exclusive prefix and writes the total to *total.
+__device__ __forceinline__ unsigned scan_buckets(unsigned v, unsigned* s_w, unsigned* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned w = lane < kBuckets / 32 ? s_w[lane] : 0u;
+        unsigned wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += u;
+        }
+        if (lane < kBuckets / 32) s_w[lane] = wi - w;     // exclusive per warp
+        if (lane == 31) *total = wi;
+    }
+    __syncthreads();
+    const unsigned r = s_w[wid] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+// Plan (one block of kBuckets threads per image): bucket b's keys go to
+// [off_b, off_b + n_b) of the image's key array (the cursor starts at off_b);
+// its work items are chunks of at most kBktChunk keys, flagged shared when
+// there are several.  The bucket counts are cleared for the next call.
+__global__ void __launch_bounds__(kBuckets) k_bkt_plan(const __grid_constant__ ReduceItems R) {
+    __shared__ unsigned s_w[kBuckets / 32];
+    __shared__ unsigned s_off[kBuckets + 1];      // first key of each bucket, then N
+    __shared__ unsigned s_item0[kBuckets + 1];    // first work item of each bucket, then all
+    __shared__ unsigned s_total;
+    const int i = blockIdx.x, b = threadIdx.x;
+    uint32_t* cnt = R.bkt_count + (size_t)i * kBuckets;
+    const unsigned nb = cnt[b];
+    cnt[b] = 0u;
+    const unsigned off = scan_buckets(nb, s_w, &s_total);
+    const unsigned n_all = s_total;
+    s_off[b] = off;
+    R.bkt_cursor[(size_t)i * kBuckets + b] = off;
+    const unsigned first = scan_buckets((nb + kBktChunk - 1) / kBktChunk, s_w, &s_total);
+    s_item0[b] = first;
+    if (b == 0) {
+        s_off[kBuckets] = n_all;
+        s_item0[kBuckets] = s_total;
+    }
+    __syncthreads();
+    const unsigned n_items = s_item0[kBuckets];
+    uint4* work = R.work + (size_t)i * R.work_stride;
+    for (unsigned t = threadIdx.x; t < n_items; t += blockDim.x) {
+        // the bucket of item t: the last q with s_item0[q] <= t (a nonempty one)
+        int lo = 0, hi = kBuckets - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_item0[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const unsigned c = t - s_item0[lo];
+        const unsigned nq = s_item0[lo + 1] - s_item0[lo];
+        const unsigned start = s_off[lo] + c * kBktChunk;
+        const unsigned len = min((unsigned)kBktChunk, s_off[lo + 1] - start);
+        work[t] = make_uint4((unsigned)lo, start, len, nq > 1 ? 1u : 0u);
+    }
+    if (threadIdx.x == 0) R.n_work[i] = (int)n_items;
+}
+
+// Pass B: each block takes tiles of kScatterPix pixels (16 consecutive pixels
+// per thread); every pixel gets its rank among the tile's pixels of its
+// bucket (a thread's run of equal buckets takes one shared-memory atomic),
+// the tile's pixels are placed in shared memory in bucket order, each
+// nonempty bucket of the tile claims a range of its run in the image's key
+// array with one global atomic, and the threads write the staged keys' low
+// 14 bits to consecutive positions of those ranges.  The per-bucket tables
+// are indexed by bslot.
+constexpr int kScatterThreads = 256;
+constexpr int kScatterPix = kScatterThreads * kGroup;      // 4096 pixels per tile
+constexpr int kScatterPer = kBuckets / kScatterThreads;    // buckets per thread in the scan
+static_assert(kBuckets % kScatterThreads == 0, "the tile scan splits the buckets evenly");
+
+__global__ void __launch_bounds__(kScatterThreads, 4)
+    k_bkt_scatter(const __grid_constant__ ReduceItems R) {
+    __shared__ unsigned s_cnt[kBuckets];      // pixels of each bucket in the tile
+    __shared__ unsigned s_base[kBuckets];     // their offset within the tile
+    __shared__ unsigned s_gpos[kBuckets];     // their first position in the key array
+    __shared__ unsigned s_w[kScatterThreads / 32];
+    __shared__ unsigned s_total;
+    __shared__ uint32_t s_key[kScatterPix];
+    const int i = item_of_block(R.first_blk, R.n_items, blockIdx.x);
+    const int g = blockIdx.x - R.first_blk[i], G = R.first_blk[i + 1] - R.first_blk[i];
+    const uint8_t* rgb = R.rgb[i];
+    const int64_t n = R.n[i];
+    const int stride = R.stride[i];
+    const bool vec = vector_ok(rgb, nullptr);
+    uint32_t* cursor = R.bkt_cursor + (size_t)i * kBuckets;
+    uint16_t* keys = R.keys16 + (size_t)i * R.keys_stride;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int b = tid; b < kBuckets; b += kScatterThreads) s_cnt[b] = 0u;
+    __syncthreads();
+    for (int64_t t0 = (int64_t)g * kScatterPix; t0 < n; t0 += (int64_t)G * kScatterPix) {
+        const int64_t p0 = t0 + (int64_t)tid * kGroup;       // this thread's 16 pixels
+        uint32_t key[kGroup];
+        int m = 0;                                            // how many are in the image
+        if (vec && p0 + kGroup <= n) {
+            pixel_keys16(rgb, p0 / kGroup, stride, key);
+            m = kGroup;
+        } else {
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                key[j] = p0 + j < n ? pixel_key(rgb, p0 + j, stride) : 0u;
+                if (p0 + j < n) m = j + 1;
+            }
+        }
+        // rank of each pixel among the tile's pixels of its bucket: walking
+        // back, each run of equal buckets takes one atomic at its last pixel
+        unsigned rank[kGroup];
+        {
+            // position of each pixel in its run, 4 bits per pixel
+            unsigned long long pos = 0;
+            unsigned p = 0;
+#pragma unroll
+            for (int j = 1; j < kGroup; ++j) {
+                p = (key[j] >> (24 - kBktBits)) == (key[j - 1] >> (24 - kBktBits)) ? p + 1u : 0u;
+                pos |= (unsigned long long)p << (4 * j);
+            }
+            unsigned base = 0;
+#pragma unroll
+            for (int j = kGroup - 1; j >= 0; --j) {
+                if (j < m) {
+                    const unsigned b = key[j] >> (24 - kBktBits);
+                    const unsigned pj = (unsigned)(pos >> (4 * j)) & 15u;
+                    const bool last = j == m - 1 ||
+                                      (j + 1 < kGroup && (key[j + 1] >> (24 - kBktBits)) != b);
+                    if (last) base = atomicAdd(&s_cnt[bslot(b)], pj + 1u);
+                    rank[j] = base + pj;
+                }
+            }
+        }
+        __syncthreads();
+        // tile offsets of the buckets in bucket order: thread t scans buckets
+        // kScatterPer t .. kScatterPer t + kScatterPer - 1
+        unsigned c[kScatterPer], sum = 0;
+#pragma unroll
+        for (int q = 0; q < kScatterPer; ++q) {
+            c[q] = s_cnt[bslot(kScatterPer * tid + q)];
+            sum += c[q];
+        }
+        unsigned incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_w[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            constexpr int kW = kScatterThreads / 32;
+            const unsigned w = lane < kW ? s_w[lane] : 0u;
+            unsigned wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned u = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+                if (lane >= o) wi += u;
+            }
+            if (lane < kW) s_w[lane] = wi - w;
+            if (lane == 31) s_total = wi;
+        }
+        __syncthreads();
+        unsigned ex = s_w[wid] + incl - sum;
+#pragma unroll
+        for (int q = 0; q < kScatterPer; ++q) {
+            const unsigned b = kScatterPer * tid + q, sl = bslot(b);
+            s_base[sl] = ex;
+            s_gpos[sl] = c[q] ? atomicAdd(cursor + b, c[q]) : 0u;
+            ex += c[q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j)
+            if (j < m) s_key[s_base[bslot(key[j] >> (24 - kBktBits))] + rank[j]] = key[j];
+        __syncthreads();
+        const unsigned tile_n = s_total;
+        for (unsigned q = tid; q < tile_n; q += kScatterThreads) {
+            const uint32_t k = s_key[q];
+            const unsigned sl = bslot(k >> (24 - kBktBits));
+            keys[s_gpos[sl] + (q - s_base[sl])] = (uint16_t)(k & (kBktBins - 1));
+        }
+#pragma unroll
+        for (int q = 0; q < kScatterPer; ++q) s_cnt[bslot(kScatterPer * tid + q)] = 0u;
+        __syncthreads();
+    }
+}
+
+// Pass C: work item (bucket b, start, length, shared) of image i counts its
+// keys in a 2^14-bin shared-memory histogram, then writes the nonzero bins
+// into the image's histogram and occupancy map: plain stores when it is the
+// bucket's only item (no other item touches those bins and words), atomics
+// when the bucket is shared.  The blocks of the launch take the items of all
+// images in turn.
+constexpr int kBktHistThreads = 512;
+
+__global__ void __launch_bounds__(kBktHistThreads, 3)
+    k_bkt_hist(const __grid_constant__ ReduceItems R, int max_items) {
+    extern __shared__ unsigned s_h[];                      // [kBktBins]
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t total = (int64_t)R.n_items * max_items;
+    for (int64_t v = blockIdx.x; v < total; v += gridDim.x) {
+        const int i = (int)(v / max_items), t = (int)(v % max_items);
+        if (t >= R.n_work[i]) continue;                    // uniform over the block
+        const uint4 w = R.work[(size_t)i * R.work_stride + t];
+        const unsigned b = w.x, start = w.y, len = w.z;
+        const bool shared = w.w != 0u;
+        const uint16_t* keys = R.keys16 + (size_t)i * R.keys_stride;
+        // the item's keys: a ragged head up to an 8-key boundary, 16-byte
+        // loads of 8 keys (at most kVec per thread, all issued before the
+        // histogram is cleared), a ragged tail
+        constexpr int kVec = kBktChunk / 8 / kBktHistThreads;
+        const unsigned a0 = min(len, (8u - (start & 7u)) & 7u);
+        const unsigned nv = (len - a0) / 8u;
+        const uint4* kv = reinterpret_cast<const uint4*>(keys + start + a0);
+        uint4 u[kVec];
+#pragma unroll
+        for (int r = 0; r < kVec; ++r) {
+            const unsigned q = tid + r * kBktHistThreads;
+            u[r] = q < nv ? __ldg(kv + q) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        const unsigned head = tid < (int)a0 ? keys[start + tid] : 0u;
+        const unsigned tq = a0 + nv * 8u + tid;
+        const unsigned tail = tq < len ? keys[start + tq] : 0u;
+        for (int q = tid; q < kBktBins / 4; q += kBktHistThreads)
+            reinterpret_cast<uint4*>(s_h)[q] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+        if (tid < (int)a0) atomicAdd(&s_h[head], 1u);
+        if (tq < len) atomicAdd(&s_h[tail], 1u);
+#pragma unroll
+        for (int r = 0; r < kVec; ++r) {
+            if (tid + r * kBktHistThreads < nv) {
+                const unsigned ws[4] = {u[r].x, u[r].y, u[r].z, u[r].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    atomicAdd(&s_h[ws[e] & 0xFFFFu], 1u);
+                    atomicAdd(&s_h[ws[e] >> 16], 1u);
+                }
+            }
+        }
+        __syncthreads();
+        uint32_t* hist = R.hist + (size_t)i * kHistBins + (size_t)b * kBktBins;
+        uint32_t* bitmap = R.bitmap + (size_t)i * kMapWords + (size_t)b * (kBktBins / 32);
+        for (int wd = wid; wd < kBktBins / 32; wd += kBktHistThreads / 32) {
+            const unsigned c = s_h[wd * 32 + lane];
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, c != 0u);
+            if (!m) continue;
+            if (shared) {
+                if (c) atomicAdd(hist + wd * 32 + lane, c);
+                if (lane == 0) atomicOr(bitmap + wd, m);
+            } else {
+                if (c) hist[wd * 32 + lane] = c;
+                if (lane == 0) bitmap[wd] = m;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -176,24 +523,63 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_emit(const __grid_constan
     }
 }
 
-// Launch the three reduction kernels for R.n_items images whose per-image
-// fields are filled in; sets the scratch pointers and the histogram blocks.
+// Mean pixels per image of a launch from which the bucketed path is used.
+constexpr int64_t kBktMinMeanPixels = 1 << 20;
+
+// Blocks of a pass over the pixels: at most `budget` blocks in all, split in
+// proportion to the images' pixels, at most `want(n)` for an image of n.
+template <typename Want>
+static void split_pixels(ReduceItems& R, int64_t budget, Want want) {
+    int64_t total = 0;
+    for (int i = 0; i < R.n_items; ++i) total += R.n[i];
+    R.first_blk[0] = 0;
+    for (int i = 0; i < R.n_items; ++i) {
+        const int64_t share = std::max<int64_t>(1, budget * R.n[i] / std::max<int64_t>(total, 1));
+        R.first_blk[i + 1] = R.first_blk[i] + (int)(R.n[i] > 0 ? std::min(want(R.n[i]), share) : 0);
+    }
+}
+
+// Launch the reduction kernels for R.n_items images whose per-image fields
+// are filled in; sets the scratch pointers and the blocks of each pass.
 static int launch_reduce(wsm_handle* h, ReduceItems& R, cudaStream_t s) {
     R.hist = h->hist;
     R.bitmap = h->bitmap;
     R.blk_total = h->blk_total;
     R.status = &h->ctrl->status;
-    int64_t total = 0;
-    for (int i = 0; i < R.n_items; ++i) total += R.n[i];
-    // at most 8 blocks of 256 per SM in all, split in proportion to pixels
-    const int64_t budget = (int64_t)h->sms * 8;
-    R.first_blk[0] = 0;
+    R.bkt_count = h->bkt_count;
+    R.bkt_cursor = h->bkt_cursor;
+    R.keys16 = h->keys16;
+    R.work = h->bkt_work;
+    R.n_work = h->bkt_nwork;
+    R.keys_stride = (int64_t)keys_stride(h);
+    R.work_stride = bkt_max_work(h->max_pixels);
+    int64_t total = 0, nmax = 0;
     for (int i = 0; i < R.n_items; ++i) {
-        const int64_t want = (R.n[i] + 255) / 256;
-        const int64_t share = std::max<int64_t>(1, budget * R.n[i] / std::max<int64_t>(total, 1));
-        R.first_blk[i + 1] = R.first_blk[i] + (int)(R.n[i] > 0 ? std::min(want, share) : 0);
+        total += R.n[i];
+        nmax = std::max(nmax, R.n[i]);
     }
-    if (R.first_blk[R.n_items] > 0) k_hist24<<<R.first_blk[R.n_items], 256, 0, s>>>(R);
+    const bool bucketed = h->reduce_path == 2 ||
+                          (h->reduce_path == 0 && total >= kBktMinMeanPixels * R.n_items);
+    if (bucketed && R.n_items > 0) {
+        static_assert(kBktBins * sizeof(unsigned) <= 64 * 1024, "bucket histogram size");
+        cudaError_t e = raise_smem_limit((const void*)k_bkt_hist, kBktBins * sizeof(unsigned));
+        if (e != cudaSuccess) return cuda_fail(e, "bucket histogram set-up");
+        // counting pass: at most 8 blocks of 256 per SM in all, 16 pixels a thread
+        split_pixels(R, (int64_t)h->sms * 8, [](int64_t n) { return (n + 4095) / 4096; });
+        if (R.first_blk[R.n_items] > 0) k_bkt_count<<<R.first_blk[R.n_items], 256, 0, s>>>(R);
+        k_bkt_plan<<<R.n_items, kBuckets, 0, s>>>(R);
+        // scatter pass: at most 4 blocks of 256 per SM in all, tiles of 4096 pixels
+        split_pixels(R, (int64_t)h->sms * 4,
+                     [](int64_t n) { return (n + kScatterPix - 1) / kScatterPix; });
+        if (R.first_blk[R.n_items] > 0)
+            k_bkt_scatter<<<R.first_blk[R.n_items], kScatterThreads, 0, s>>>(R);
+        k_bkt_hist<<<h->sms * 3, kBktHistThreads, kBktBins * sizeof(unsigned), s>>>(
+            R, (int)bkt_max_work(nmax));
+    } else {
+        // at most 8 blocks of 256 per SM in all, one pixel a thread and step
+        split_pixels(R, (int64_t)h->sms * 8, [](int64_t n) { return (n + 255) / 256; });
+        if (R.first_blk[R.n_items] > 0) k_hist24<<<R.first_blk[R.n_items], 256, 0, s>>>(R);
+    }
     k_scan_count<<<kScanBlocks * R.n_items, kScanThreads, 0, s>>>(R);
     k_scan_emit<<<kScanBlocks * R.n_items, kScanThreads, 0, s>>>(R);
     cudaError_t e = cudaGetLastError();
@@ -302,5 +688,13 @@ extern "C" int wsm_reduce_batch(wsm_handle* h, wsm_item* items, int n_items, wsm
     rc = read_status(h, s);
     if (rc != WSM_OK) return rc;
     for (int i = 0; i < n_items; ++i) items[i].n_unique = h->host_nu[i];
+    return WSM_OK;
+}
+
+extern "C" int wsm_set_reduce_path(wsm_handle* h, int path) {
+    int rc = check_handle(h);
+    if (rc != WSM_OK) return rc;
+    if (path < 0 || path > 2) return fail(WSM_E_INVAL, "path must be 0, 1 or 2");
+    h->reduce_path = path;
     return WSM_OK;
 }

@@ -25,3 +25,16 @@ def read_golden(name: str) -> list[list[str]]:
             if line and not line.startswith("#"):
                 rows.append(line.split())
     return rows
+
+
+def pytest_terminal_summary(terminalreporter):
+    """List the whole runs the GPU parity tests compared with the oracle and
+    the pass at which each first met a decision taken by FP32 rounding."""
+    mod = sys.modules.get("parity")
+    if mod is None or not mod.RUNS:
+        return
+    terminalreporter.section("whole-path parity runs (GPU vs oracle)")
+    for name, it_g, it_o, div, rel in mod.RUNS:
+        where = "no divergence" if div is None else f"first rounding decision at pass {div}"
+        terminalreporter.write_line(f"{name}: iterations {it_g}/{it_o}, {where}, "
+                                    f"free-run MSE relative difference {rel:.2e}")

@@ -171,6 +171,36 @@ def test_reduce_init_distortion_batch_equal_single_calls(wsm):
         assert np.array_equal(batch[q]["counts"][:nus[q]].cpu().numpy(), ref_counts)
 
 
+@pytest.mark.parametrize("path", [1, 2])
+def test_reduce_batch_both_paths_match_the_oracle(wsm, path):
+    """A reduction launch of 5 images of uneven sizes (one empty-ish in colors,
+    one 4-byte, one unaligned size) through either way of filling the
+    histograms, image by image against the oracle."""
+    imgs = [synth.image(1024, 768, 71, 20), synth.image(333, 517, 72, 3),
+            np.full((64, 64, 3), 9, np.uint8), synth.image(1500, 1100, 73, 11),
+            np.concatenate([synth.image(257, 263, 74, 7), np.full((257, 263, 1), 1, np.uint8)],
+                           -1)]
+    with wsm.Handle(256, 1500 * 1100) as h:
+        wsm.wsm_reserve_batch(h, len(imgs))
+        wsm.wsm_set_reduce_path(h, path)
+        batch = []
+        for img in imgs:
+            n = img.shape[0] * img.shape[1]
+            batch.append(dict(rgb=torch.from_numpy(np.ascontiguousarray(img)).cuda(),
+                              colors=torch.empty(n, dtype=torch.uint32, device="cuda"),
+                              counts=torch.empty(n, dtype=torch.uint32, device="cuda"),
+                              labels=torch.empty(n, dtype=torch.uint8, device="cuda"),
+                              index=torch.empty(img.shape[:2], dtype=torch.uint8,
+                                                device="cuda")))
+        for _ in range(2):                  # the second launch reuses the cleared scratch
+            nus = wsm.wsm_reduce_batch(h, batch)
+            for q, img in enumerate(imgs):
+                rc, rn = oracle.unique(img)
+                assert nus[q] == len(rc)
+                assert np.array_equal(batch[q]["colors"][:nus[q]].cpu().numpy(), rc)
+                assert np.array_equal(batch[q]["counts"][:nus[q]].cpu().numpy(), rn)
+
+
 def test_quantize_batch_equals_quantize(wsm):
     imgs = [synth.image(hh, ww, 40 + q, 3 + 4 * q) for q, (hh, ww) in
             enumerate([(256, 256), (120, 200), (64, 48)])]

@@ -16,13 +16,15 @@ checks, image by image, what holds at any size:
 and, on sampled images, that the batch launch gives bit for bit what the
 one-image calls give, and that its last pass is the oracle's Algorithm 2
 pass from the same state (teacher forcing, as in the small-size tests).
+The 8 sweep images of the benchmark's step are also compared with the
+oracle's whole runs (tests/parity.py).
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle
-from test_gpu_parity import GAP, check_pass, gpu_pass
+from parity import GAP, check_pass, compare_whole_path, gpu_pass
 
 pytestmark = pytest.mark.gpu
 
@@ -85,10 +87,20 @@ def check_image(img, res):
 
 
 def test_sweep_512_as_benchmarked(wsm, workloads):
+    """The benchmark's own step (the 8 sweep images at the benchmark's seeds,
+    autotuned shape, three captured graphs): each image's results against the
+    oracle's whole run (tests/parity.py: the run while it agrees with the
+    oracle's, teacher forcing after a rounding decision, the final MSE from
+    the oracle's palette within 1e-5)."""
     images, seeds = workloads["sweep"]
     plan = run_as_benchmarked(wsm, images, seeds)
-    for q, img in enumerate(images):
-        check_image(img, plan.result(q))
+    with wsm.Handle(K, 1 << 18, 1 << 18) as h:
+        for q, img in enumerate(images):
+            res = plan.result(q)
+            check_image(img, res)
+            _, _, div, mse_rel = compare_whole_path(wsm, h, img, K, seeds[q], ITERS, 0.0,
+                                                    got=res, name=f"bench sweep{q} K={K}")
+            assert mse_rel <= (1e-5 if div is None else 1e-4), (q, div, mse_rel)
 
 
 def test_uneven_batch_to_2048_as_benchmarked(wsm, workloads):

@@ -1,17 +1,15 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Bars (Celebi, arXiv:1011.0093; tolerances of the FP32-vs-FP64 contract):
-  - unique colors, counts, initial indices, integer cluster sums S_k / W_k,
-    distance counts and the index image: bit-exact;
-  - memberships: bit-exact except for colors whose best and second-best
-    squared distances differ by at most 1e-3 in the oracle (a near-tie that
-    FP32 may resolve the other way);
-  - centers: the GPU stores fl32(S_k / W_k), so when the sums agree its
-    centers equal the oracle's FP64 centers rounded to FP32 exactly, and
-    always lie within 1e-4 of them;
-  - SSE and MSE: within 1e-5 relative.
-Near-ties are handled by teacher forcing: every iteration starts the GPU from
-the oracle's centers and memberships, so one flipped tie cannot carry over.
+The bars and the rule for memberships that may differ are those of
+tests/parity.py (Celebi, arXiv:1011.0093, Algorithm 2): unique colors,
+counts, initial centers, integer sums, the index image and, where the
+arithmetic is exact, every membership (exact ties included) and Algorithm
+2's distance count are bit-exact; a membership differs only where FP32
+rounding can decide it; centers within 1e-4 (fl32(S/W) where the sums
+agree), SSE and MSE within 1e-5 relative.  Teacher forcing starts every
+compared GPU pass from the oracle's state, so one rounding decision cannot
+carry over; whole runs are compared free-running until the first such
+decision and in teacher forcing after it.
 """
 import numpy as np
 import pytest
@@ -19,10 +17,9 @@ import torch
 
 import oracle
 import synth
+from parity import compare_whole_path, dev, exact_ties, pad4, teacher_forced, unexplained_flips
 
 pytestmark = pytest.mark.gpu
-
-GAP = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -41,10 +38,6 @@ def h(wsm):
         yield handle
 
 
-def dev(a):
-    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
-
-
 def gpu_unique(wsm, h, img):
     n = img.shape[0] * img.shape[1] if img.ndim == 3 else 0
     colors = torch.empty(max(n, 1), dtype=torch.uint32, device="cuda")
@@ -53,30 +46,13 @@ def gpu_unique(wsm, h, img):
     return colors[:nu], counts[:nu], nu
 
 
-def pad4(c):
-    out = np.zeros((c.shape[0], 4), np.float32)
-    out[:, :3] = c
-    return out
-
-
-def f32_centers(S, W, fallback):
-    """fl32 of the exact quotient S/W (the oracle's FP64 quotient rounded)."""
-    c = np.array(fallback, np.float64).copy()
-    nz = W > 0
-    c[nz] = S[nz].astype(np.float64) / W[nz, None].astype(np.float64)
-    return c.astype(np.float32)
-
-
-def gaps(colors, centers):
-    best, second, _ = oracle.exhaustive(colors, centers)
-    return second - best
-
-
 # ---- unique colors and counts --------------------------------------------------
 
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("case", ["plain256", "sweep0", "sweep3", "sweep7", "ragged", "stride4",
                                   "single_pixel", "one_color", "tiny_levels", "wide"])
-def test_reduce_bit_exact(wsm, h, case):
+def test_reduce_bit_exact(wsm, h, case, path):
+    """Both ways of filling the histogram (direct atomics, bucketed), forced."""
     img = {
         "plain256": synth.plain_256,
         "sweep0": lambda: synth.sweep_512_one(0),
@@ -90,11 +66,32 @@ def test_reduce_bit_exact(wsm, h, case):
         "tiny_levels": lambda: synth.tiny(33, 31, 2, 4),
         "wide": lambda: synth.image(16, 2048, 12, 20),
     }[case]()
-    c, n, nu = gpu_unique(wsm, h, img)
+    wsm.wsm_set_reduce_path(h, path)
+    try:
+        c, n, nu = gpu_unique(wsm, h, img)
+    finally:
+        wsm.wsm_set_reduce_path(h, 0)
     rc, rn = oracle.unique(img)
     assert nu == len(rc)
     assert np.array_equal(c.cpu().numpy(), rc)
     assert np.array_equal(n.cpu().numpy(), rn)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_reduce_large_flat_and_noisy_regions(wsm, h, path):
+    """A 2048x2048 image whose left half is one color and right half noise:
+    one bucket holds millions of pixels (split into many work items of the
+    bucketed path) beside thousands of small buckets."""
+    img = synth.image(2048, 2048, 33, 18)
+    img[:, :1024] = (200, 40, 90)
+    wsm.wsm_set_reduce_path(h, path)
+    try:
+        c, n, nu = gpu_unique(wsm, h, img)
+    finally:
+        wsm.wsm_set_reduce_path(h, 0)
+    rc, rn = oracle.unique(img)
+    assert nu == len(rc) and n.cpu().numpy().max() >= 2048 * 1024
+    assert np.array_equal(c.cpu().numpy(), rc) and np.array_equal(n.cpu().numpy(), rn)
 
 
 def test_reduce_every_24bit_color_once(wsm, h):
@@ -166,59 +163,6 @@ def test_init_all_colors_and_too_many(wsm, h):
 
 # ---- the Sort-Means iterations, teacher-forced ----------------------------------
 
-def check_pass(colors, counts, c, lab, got_labels, got_centers, got_S, got_W, got_sse,
-               got_ev, it, paper_scan=True):
-    """Compare one GPU pass with one oracle pass started from the same state
-    (oracle centers c, memberships lab).  Returns the oracle's pass and the
-    number of colors whose membership differs (each must be a near-tie)."""
-    step = oracle.iteration(colors, counts, c, lab)
-    g = gaps(colors, c)
-    diff = got_labels != step["labels"]
-    assert np.all(g[diff] <= GAP), (it, np.flatnonzero(diff)[:5], g[diff][:5])
-    assert abs(got_sse - step["sse"]) <= 1e-5 * step["sse"], (it, got_sse, step["sse"])
-    # clusters that no flipped color left or joined must match bit for bit
-    touched = np.zeros(c.shape[0], bool)
-    touched[got_labels[diff]] = True
-    touched[step["labels"][diff]] = True
-    ok = ~touched
-    assert np.array_equal(got_S[ok], step["S"][ok]) and np.array_equal(got_W[ok], step["W"][ok])
-    expect = f32_centers(step["S"], step["W"], c)
-    assert np.array_equal(got_centers[ok], expect[ok]), it
-    assert np.abs(got_centers[ok] - step["centers"][ok]).max(initial=0.0) <= 1e-4
-    if paper_scan and it == 0 and not diff.any():   # integer centers: exact FP32 distances
-        assert got_ev == step["evaluated"]
-    return step, int(diff.sum())
-
-
-def gpu_pass(wsm, h, cd, nd, nu, K, centers, labels):
-    done, trace = wsm.wsm_iterate(h, cd, nd, nu, K, centers, labels, 1, 0.0)
-    assert done == 1
-    ev, S, W = wsm.wsm_iterate_stats(h, K)
-    return (labels.cpu().numpy(), centers.cpu().numpy()[:, :3], S.numpy(), W.numpy(), trace[0],
-            ev)
-
-
-def teacher_forced(wsm, h, img, K, seed, iters, paper_scan=False):
-    """Run `iters` oracle passes; before each, start the GPU from the
-    oracle's centers and memberships and compare one GPU pass with it.  Each
-    GPU pass is the first pass of its launch, so it uses the candidate start
-    unless paper_scan, which also checks the distance counts of Algorithm 2."""
-    wsm.wsm_set_first_pass_start(h, not paper_scan)
-    colors, counts = oracle.unique(img)
-    cd, nd = dev(colors), dev(counts)
-    c, lab = oracle.init(colors, K, seed)
-    flips = 0
-    for it in range(iters):
-        centers = dev(pad4(c.astype(np.float32)))
-        labels = dev(lab.astype(np.int16 if h.wide else np.uint8))
-        out = gpu_pass(wsm, h, cd, nd, len(colors), K, centers, labels)
-        step, nflip = check_pass(colors, counts, c, lab, *out, it, paper_scan)
-        flips += nflip
-        c, lab = step["centers"], step["labels"]
-    wsm.wsm_set_first_pass_start(h, True)
-    return flips
-
-
 def test_iterations_teacher_forced_plain256(wsm, h):
     flips = teacher_forced(wsm, h, synth.plain_256(), 16, 0, 40)
     assert flips <= 5
@@ -236,14 +180,36 @@ def test_visits_and_counts_follow_algorithm_2_without_the_candidate_start(wsm, h
     teacher_forced(wsm, h, img_fn(), K, 3, passes, paper_scan=True)
 
 
+@pytest.mark.parametrize("paper_scan", [False, True])
+@pytest.mark.parametrize("s,K", [(1, 256), (4, 64), (6, 32)])
+def test_exact_arithmetic_every_membership_and_count(wsm, h, s, K, paper_scan):
+    """Passes from centers on the 1/8 grid, where FP32 and FP64 compute every
+    distance exactly: every membership, exact ties included, must be the one
+    Algorithm 2's visit order gives (the later of equal distances), and with
+    the paper's start the distance count must be Algorithm 2's."""
+    flips = teacher_forced(wsm, h, synth.sweep_512_one(s), K, 40 + s, 6, paper_scan=paper_scan,
+                           exact=True)
+    assert flips == 0
+
+
 def test_iterations_teacher_forced_ties(wsm, h):
-    """Few levels per channel: exact distance ties everywhere, integer
-    centers in the first pass, duplicate centers possible."""
+    """Few levels per channel: exact distance ties everywhere, duplicate
+    centers possible.  From the FP32-rounded oracle state every difference
+    must be explained by rounding; from centers on the 1/8 grid (exact
+    arithmetic) there must be none, in both start modes, and the passes must
+    meet exact ties."""
+    met = 0
     for seed in range(6):
         img = synth.tiny(40, 37, 50 + seed, 4)
-        colors, _ = oracle.unique(img)
-        teacher_forced(wsm, h, img, min(len(colors), 5 + 3 * seed), seed, 6)
-        teacher_forced(wsm, h, img, min(len(colors), 5 + 3 * seed), seed, 6, paper_scan=True)
+        colors, counts = oracle.unique(img)
+        K = min(len(colors), 5 + 3 * seed)
+        teacher_forced(wsm, h, img, K, seed, 6)
+        teacher_forced(wsm, h, img, K, seed, 6, paper_scan=True)
+        assert teacher_forced(wsm, h, img, K, seed, 6, exact=True) == 0
+        assert teacher_forced(wsm, h, img, K, seed, 6, paper_scan=True, exact=True) == 0
+        c, lab = oracle.init(colors, K, seed)
+        met += exact_ties(colors, c, lab)
+    assert met > 0
 
 
 # ---- free-running: whole path vs the oracle's whole path --------------------------
@@ -254,70 +220,37 @@ def run_gpu(wsm, h, img, K, seed, max_iter, eps):
     return q
 
 
-def compare_whole_path(wsm, h, img, K, seed, max_iter, eps):
-    """One wsm.quantize call against oracle.quantize.  The GPU run is replayed
-    pass by pass from its own state next to the oracle: while memberships
-    agree, every pass must match as in teacher forcing; the first pass where
-    they differ must differ only at near-ties, after which the two runs may
-    legitimately drift apart and only the replay's agreement with the
-    one-call run is checked.  Without such a divergence the final centers,
-    SSE trace, MSE and index image must match the oracle's."""
-    q = run_gpu(wsm, h, img, K, seed, max_iter, eps)
-    ref = oracle.quantize(img, K, seed, max_iter, eps)
-    colors, counts = ref["colors"], ref["counts"]
-    assert q.n_unique == len(colors)
-    assert np.array_equal(q.colors.cpu().numpy(), colors)
-    assert np.array_equal(q.counts.cpu().numpy(), counts)
-    # replay: the GPU one pass at a time from its own state
-    cd, nd = dev(colors), dev(counts)
-    centers = torch.empty((K, 4), dtype=torch.float32, device="cuda")
-    labels = torch.empty(len(colors), dtype=torch.int16 if h.wide else torch.uint8, device="cuda")
-    wsm.wsm_init(h, cd, len(colors), K, seed, centers, labels)
-    c, lab = oracle.init(colors, K, seed)
-    diverged = None
-    gpu_trace = []
-    for it in range(q.iters):
-        out = gpu_pass(wsm, h, cd, nd, len(colors), K, centers, labels)
-        gpu_trace.append(out[4])
-        if diverged is None:
-            step, nflip = check_pass(colors, counts, c, lab, *out, it, paper_scan=False)
-            if nflip:
-                diverged = it
-            c, lab = step["centers"], step["labels"]
-    # the replay reproduces the one-call run exactly
-    assert gpu_trace == list(q.sse_trace)
-    assert torch.equal(centers, q.centers)
-    if diverged is not None:
-        return q, ref, diverged
-    assert q.iters == ref["iters"], (q.iters, ref["iters"])
-    tr = np.array(q.sse_trace)
-    assert np.all(np.abs(tr - ref["sse_trace"]) <= 1e-5 * ref["sse_trace"])
-    gc = q.centers.cpu().numpy()[:, :3]
-    assert np.abs(gc - ref["centers"]).max() <= 1e-4
-    assert abs(q.mse - ref["mse"]) <= 1e-5 * ref["mse"]
-    # index image: bit-exact except at pixels whose color is a near-tie for
-    # the final centers
-    g = gaps(colors, ref["centers"])
-    glab = q.labels.cpu().numpy()
-    diff = glab != ref["labels"]
-    assert np.all(g[diff] <= GAP)
-    keys = ((img[..., 0].astype(np.uint32) << 16) | (img[..., 1].astype(np.uint32) << 8)
-            | img[..., 2]).ravel()
-    clear = np.isin(keys, colors[~diff])
-    assert np.array_equal(q.index.cpu().numpy().ravel()[clear], ref["index"][clear])
-    return q, ref, None
-
-
 def test_whole_path_plain256_convergent(wsm, h):
-    q, ref, div = compare_whole_path(wsm, h, synth.plain_256(), 16, 0, 100, 1e-4)
-    assert div is None and 2 <= q.iters < 100
+    got, ref, div, _ = compare_whole_path(wsm, h, synth.plain_256(), 16, 0, 100, 1e-4,
+                                          name="plain256 K=16 WSM-C")
+    assert div is None and 2 <= got["iters"] < 100
 
 
 @pytest.mark.parametrize("s", range(8))
 def test_whole_path_sweep512_fixed10(wsm, h, s):
+    """WSM (10 iterations) on every sweep image and K: the run itself while it
+    agrees with the oracle's, teacher forcing after a rounding decision, and
+    the final MSE from the oracle's palette within 1e-5; the free runs' MSEs
+    must stay within 1e-4 of each other (relative) even after a divergence."""
     img = synth.sweep_512_one(s)
     for K in (32, 64, 128, 256):
-        compare_whole_path(wsm, h, img, K, 1000 * s + K, 10, 0.0)
+        got, ref, div, mse_rel = compare_whole_path(wsm, h, img, K, 1000 * s + K, 10, 0.0,
+                                                    name=f"sweep{s} K={K} WSM")
+        assert mse_rel <= (1e-5 if div is None else 1e-4), (K, div, mse_rel)
+
+
+@pytest.mark.parametrize("s", [1, 3, 5, 7])
+def test_whole_path_sweep512_convergent(wsm, h, s):
+    """WSM-C (Sec. 3.2 stop rule, eps = 1e-4, at most 100 iterations) on four
+    sweep images at K = 32 and 256: the GPU's fixed-point SSE stop rule must
+    stop at the oracle's iteration while the runs agree."""
+    img = synth.sweep_512_one(s)
+    for K in (32, 256):
+        got, ref, div, mse_rel = compare_whole_path(wsm, h, img, K, 500 + s + K, 100, 1e-4,
+                                                    name=f"sweep{s} K={K} WSM-C")
+        if div is None:
+            assert got["iters"] == ref["iters"]
+        assert 2 <= ref["iters"] < 100
 
 
 # ---- palettes of more than 256 colors: 16-bit memberships ----------------------------
@@ -342,10 +275,10 @@ def test_wide_palette_visits_follow_algorithm_2(wsm, hw):
 def test_wide_palette_whole_path(wsm, hw, s, K):
     """Init, iterations, final mapping and MSE with uint16 memberships and
     index image, against the oracle."""
-    q, ref, div = compare_whole_path(wsm, hw, synth.sweep_512_one(s), K, 77 + s, 10, 0.0)
-    assert q.index.dtype == torch.int16 and q.labels.dtype == torch.int16
-    if div is None:
-        assert int(q.index.max()) >= 256          # labels past one byte were written
+    got, ref, div, _ = compare_whole_path(wsm, hw, synth.sweep_512_one(s), K, 77 + s, 10, 0.0,
+                                          name=f"sweep{s} K={K} wide")
+    assert got["index"].dtype == torch.int16 and got["labels"].dtype == torch.int16
+    assert int(got["index"].max()) >= 256          # labels past one byte were written
 
 
 def test_wide_palette_batch_equals_single(wsm, hw):
@@ -385,9 +318,9 @@ def test_map_and_distortion_given_labels(wsm, h):
     index = torch.empty(img.shape[:2], dtype=torch.uint8, device="cuda")
     wsm.wsm_map(h, dev(img), dev(colors), len(colors), centers, K, labels, index)
     got_lab = labels.cpu().numpy()
-    g = gaps(colors, pal.astype(np.float64))
-    diff = got_lab != lab
-    assert np.all(g[diff] <= GAP)
+    p64 = pal.astype(np.float64)
+    again, _, _ = oracle.assign(colors, p64, lab)           # the oracle from the same start
+    assert unexplained_flips(colors, p64, p64, lab, got_lab, again).size == 0
     expect = oracle.map_pixels(img, colors, got_lab.astype(np.int32))
     assert np.array_equal(index.cpu().numpy().ravel(), expect)
     m = wsm.wsm_distortion(h, dev(img), centers, K, index)
@@ -410,14 +343,18 @@ def test_unaligned_buffers_take_the_byte_path(wsm, h):
     n = img.shape[0] * img.shape[1]
     K = 32
     c_al, w_al, nu = gpu_unique(wsm, h, img)
-    for off in (1, 3, 8):
+    for off, path in ((1, 1), (3, 1), (8, 1), (1, 2), (5, 2)):
         buf = torch.zeros(3 * n + 16, dtype=torch.uint8, device="cuda")
         rgb = buf[off:off + 3 * n].view(img.shape)
         rgb.copy_(dev(img))
         assert rgb.data_ptr() % 16 == off % 16
         colors = torch.empty(n, dtype=torch.uint32, device="cuda")
         counts = torch.empty(n, dtype=torch.uint32, device="cuda")
-        assert wsm.wsm_reduce(h, rgb, colors, counts) == nu
+        wsm.wsm_set_reduce_path(h, path)
+        try:
+            assert wsm.wsm_reduce(h, rgb, colors, counts) == nu
+        finally:
+            wsm.wsm_set_reduce_path(h, 0)
         assert torch.equal(colors[:nu], c_al) and torch.equal(counts[:nu], w_al)
     colors, counts = oracle.unique(img)
     c0, lab0 = oracle.init(colors, K, 5)
@@ -464,7 +401,7 @@ def test_round_palette_and_the_mse_of_the_8bit_palette(wsm, h):
 
 def test_k1_and_lossless(wsm, h):
     img = synth.image(50, 40, 6, 3)
-    compare_whole_path(wsm, h, img, 1, 0, 5, 0.0)
+    compare_whole_path(wsm, h, img, 1, 0, 5, 0.0, name="50x40 K=1")
     tiny = synth.tiny(8, 8, 2, 3)
     nu = len(oracle.unique(tiny)[0])
     q = run_gpu(wsm, h, tiny, nu, 5, 10, 1e-4)
@@ -501,7 +438,7 @@ def test_bad_labels_and_indices_reported(wsm, h):
     index = torch.full((64, 64), 9, dtype=torch.uint8, device="cuda")
     with pytest.raises(wsm.WsmError, match="INVAL"):
         wsm.wsm_distortion(h, dev(img), centers, 8, index)
-    compare_whole_path(wsm, h, img, 8, 1, 5, 0.0)        # handle still usable
+    compare_whole_path(wsm, h, img, 8, 1, 5, 0.0, name="64x64 K=8 after bad labels")
 
 
 def test_async_calls_then_status(wsm, h):

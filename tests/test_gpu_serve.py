@@ -1,7 +1,9 @@
 """The native serving loop (wsm_server_*): continuous batching over lanes,
 admission by device-memory footprint, and results that are the same for a
 request alone and in a mix of other requests -- bit for bit, and equal to
-the one-image path (quantize)."""
+the one-image path (quantize) -- and that match the oracle's whole run
+(Celebi, arXiv:1011.0093, Algorithm 2 per request) under the rules of
+tests/parity.py."""
 import threading
 
 import numpy as np
@@ -9,6 +11,7 @@ import pytest
 import torch
 
 import synth
+from parity import compare_whole_path
 
 pytestmark = pytest.mark.gpu
 
@@ -113,3 +116,39 @@ def test_settings_failures_and_concurrent_submitters(wsm):
         res = {q: srv.wait(p) for q, p in out.items()}
     for q, (img, K, s, it, eps) in enumerate(jobs):
         assert same(res[q], one_image_path(wsm, img, K, s, it, eps)), q
+
+
+def test_served_results_match_the_oracle(wsm):
+    """Requests of each palette size the server is driven with (K = 16, 64,
+    256), one of them of the largest size the server admits (4096 x 4096),
+    submitted in a mix with other requests, each compared with the oracle's
+    whole run of its image, K and seed: N', the palette and iteration count
+    while the runs agree, every pixel's index (its color's membership), the
+    index image and the MSE (tests/parity.py)."""
+    checks = [(synth.image(4096, 4096, 91, 8), 256, 17),
+              (synth.image(300, 260, 92, 9), 16, 5),
+              (synth.image(512, 384, 93, 14), 64, 6),
+              (synth.sweep_512_one(4), 256, 7)]
+    others = mix(24, 300)
+    with wsm.Server(lanes=2, slots_per_lane=8, arena_bytes=2 << 30) as srv:
+        pend = []
+        for q, (img, k, s) in enumerate(others):
+            pend.append((srv.submit(pinned(img), k, s), None))
+            if q % 6 == 2:
+                img_c, k_c, s_c = checks[q // 6]
+                pend.append((srv.submit(pinned(img_c), k_c, s_c), q // 6))
+        results = [(srv.wait(p), m) for p, m in pend]
+        st = srv.stats()
+    assert st["failed"] == 0 and st["max_in_flight"] > 1
+    seen = set()
+    with wsm.Handle(256, 1 << 24, 1 << 24) as h:
+        for res, m in results:
+            if m is None:
+                continue
+            img, K, seed = checks[m]
+            got = dict(centers=res["palette"], iters=res["iters"], mse=res["mse"],
+                       index=res["index"], n_unique=res["n_unique"])
+            compare_whole_path(wsm, h, img, K, seed, 10, 0.0, got=got,
+                               name=f"served {img.shape[0]}x{img.shape[1]} K={K}")
+            seen.add(m)
+    assert seen == set(range(len(checks)))
