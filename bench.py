@@ -77,7 +77,7 @@ L2_FLUSH_BYTES = 256 << 20
 # per launch), init, the plan kernel (which also clears the launch's counters)
 # and the sort-means launch (which also writes N' and the iteration counts) for
 # the iterations, the plan kernel, the map-mode sort-means launch (which also
-# sums the squared errors), the gather and the MSE kernel (up to 48 images per
+# sums the squared errors), the gather and the MSE kernel (up to 64 images per
 # launch)
 KERNELS_PER_STEP = 10
 

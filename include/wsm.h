@@ -211,7 +211,7 @@ typedef struct {
 WSM_API int wsm_reserve_batch(wsm_handle* h, int max_items);
 
 /* Algorithm 2 with the Sec. 3.2 termination rule for n_items independent
- * images in one persistent cooperative launch per 48 images: the blocks are
+ * images in one persistent cooperative launch per 64 images: the blocks are
  * split into one group per image (in proportion to its unique colors and
  * palette size), each group iterating its image exactly as wsm_iterate would
  * (same results, bit for bit) with a barrier of its own, so images of
@@ -235,7 +235,7 @@ WSM_API int wsm_reduce_batch(wsm_handle* h, wsm_item* items, int n_items, wsm_st
 /* Algorithm 2, first step, for n_items images, as wsm_init would do them
  * one by one with seeds[i] (same centers and labels): the host draws every
  * image's K indices (Floyd sampling of splitmix64 draws), one copy moves
- * them to the device and one launch per 48 images gathers the centers and
+ * them to the device and one launch per 64 images gathers the centers and
  * zeroes the labels.  seeds: host uint64 [n_items].  Waits, on the host,
  * only for the previous call's index copy.
  * Errors: WSM_E_INVAL (K, n_unique < K, pointers, more items than slots). */
@@ -244,7 +244,7 @@ WSM_API int wsm_init_batch(wsm_handle* h, const wsm_item* items, int n_items,
 
 /* Eq. 2 for n_items images, as wsm_distortion gives them one by one (same
  * values: the sum is exact in 2^-20 units whatever the block split), in one
- * pair of launches per 48 images.
+ * pair of launches per 64 images.
  *   d_mse  device double [n_items] (may be NULL)
  *   mse    host double [n_items] (may be NULL; if given, synchronises and
  *          reports a palette index >= K as WSM_E_INVAL)
@@ -484,7 +484,7 @@ typedef struct {
     int max_K;               /* 1..256 */
     int64_t max_pixels;      /* per request, 1..2^24 */
     int lanes;               /* 1..8 */
-    int slots_per_lane;      /* 1..48 */
+    int slots_per_lane;      /* 1..64 */
     int64_t arena_bytes;     /* device memory for the requests' buffers */
 } wsm_server_config;
 

@@ -32,7 +32,7 @@ constexpr int kScanBlocks = kMapWords / kScanWordsPerBlock;             // 256
 constexpr int kMaxTrace = 4096;              // SSE values kept per wsm_iterate call
 constexpr int kCopies = 4;                   // replicas of the global accumulators
 constexpr int kChunk = 32;                   // colors per warp chunk (one per lane)
-constexpr int kMaxBatch = 48;                // images per persistent launch
+constexpr int kMaxBatch = 64;                // images per persistent launch
 constexpr int kReduceSlots = 16;             // images per unique-color reduction launch
 constexpr int kGridCells = 4096;             // 16^3 cells of the first pass's candidate grid
 // Bucketed unique-color reduction (large images): buckets by the top 10 bits

@@ -306,7 +306,7 @@ extern "C" int wsm_server_create(wsm_server** out, const wsm_server_config* cfg)
         return fail(WSM_E_INVAL, "max_pixels must be in [1, 2^24]");
     if (cfg->lanes < 1 || cfg->lanes > 8) return fail(WSM_E_INVAL, "lanes must be in [1, 8]");
     if (cfg->slots_per_lane < 1 || cfg->slots_per_lane > kMaxBatch)
-        return fail(WSM_E_INVAL, "slots_per_lane must be in [1, 48]");
+        return fail(WSM_E_INVAL, "slots_per_lane must be in [1, 64]");
     if (cfg->arena_bytes < ((int64_t)1 << 20)) return fail(WSM_E_INVAL, "arena_bytes below 1 MiB");
     wsm_server* S = new (std::nothrow) wsm_server();
     if (!S) return fail(WSM_E_NOMEM, "host allocation failed");

@@ -67,7 +67,7 @@ def quantize_batch(images: list, K: int, seeds: list, max_iter: int = 10, eps: f
                    handle: N.Handle | None = None, mse: bool = True, stream=None) -> list:
     """Quantize several uint8 [H, W, 3|4] CUDA images to K colors each: one
     batched call per step of the path (unique colors, initialisation, the
-    Sort-Means iterations in one persistent launch per 48 images, mapping,
+    Sort-Means iterations in one persistent launch per 64 images, mapping,
     MSE), with the results of quantize() image by image."""
     if handle is None:
         biggest = max(int(im.shape[0]) * int(im.shape[1]) for im in images)

@@ -80,9 +80,9 @@ def test_batch_equals_single_calls(wsm, max_iter, eps):
 
 
 def test_batch_matches_oracle_and_more_than_one_launch(wsm):
-    """A batch of 50 small images spans two launches (48 per launch); each
+    """A batch of 70 small images spans two launches (64 per launch); each
     image's index image matches the oracle's wherever no near-tie decides."""
-    specs = [(48 + (q % 7) * 8, 40 + (q % 5) * 8, 200 + q, q % 9, 4 + (q % 13)) for q in range(50)]
+    specs = [(48 + (q % 7) * 8, 40 + (q % 5) * 8, 200 + q, q % 9, 4 + (q % 13)) for q in range(70)]
     imgs = [synth.image(hh, ww, seed, noise) for hh, ww, seed, noise, _ in specs]
     with wsm.Handle(64, 112 * 72) as h:
         wsm.wsm_reserve_batch(h, len(specs))

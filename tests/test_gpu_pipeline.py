@@ -151,12 +151,12 @@ def test_autotune_then_graph_replay_on_new_pixels(wsm):
 
 
 def test_more_than_one_launch_of_each_kernel(wsm):
-    """50 images: four reduction launches (16 per launch) and two persistent
-    launches (48 per launch) per step."""
-    imgs = [synth.image(40 + (q % 6) * 8, 48 + (q % 4) * 8, 6000 + q, q % 13) for q in range(50)]
+    """70 images: five reduction launches (16 per launch) and two persistent
+    launches (64 per launch) per step."""
+    imgs = [synth.image(40 + (q % 6) * 8, 48 + (q % 4) * 8, 6000 + q, q % 13) for q in range(70)]
     Ks = [min(4 + (q % 3) * 6, len(np.unique(i.reshape(-1, 3), axis=0)))
           for q, i in enumerate(imgs)]
-    seeds = [q * 31 for q in range(50)]
+    seeds = [q * 31 for q in range(70)]
     plan = wsm.BatchPlan([i.shape for i in imgs], Ks, seeds, max_iter=8)
     plan.load([torch.from_numpy(i) for i in imgs])
     plan.run()
