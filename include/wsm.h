@@ -436,8 +436,8 @@ WSM_API int wsm_set_first_pass_start(wsm_handle* h, int candidate);
 
 /* How the handle's unique-color reductions fill their histogram (Sec. 2,
  * data sampling; both give the same colors and counts bit for bit):
- *   0  by size (default): bucketed when a launch's images have at least 2^20
- *      pixels on average, direct otherwise;
+ *   0  by size (default): bucketed when a launch has at least 2^24 pixels
+ *      in all and 2^21 per image on average, direct otherwise;
  *   1  direct: one global atomic per pixel into the 2^24-bin histogram (lanes
  *      of a warp with the same color combined);
  *   2  bucketed: pixels grouped by the top 10 bits of their color, then each
