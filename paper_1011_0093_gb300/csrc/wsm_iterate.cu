@@ -669,32 +669,47 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
         if (!grid_sync(&ctrl->bar_count, P.status, G)) return;
 
         // ---------------- phase A: totals, centers, stop rule, next table ----------------
+        // Every load of the totals a thread needs is issued before any is
+        // used: right after the barrier they come from L2 lines that all
+        // blocks of the group have just updated, and a chain of dependent
+        // rounds of loads costs microseconds.
+        unsigned long long fx = 0, evt = 0, N = 0, nz = 0;
+        if (wid == 0 && lane < kCopies) {
+            const unsigned long long* s64 = sums64 + (size_t)buf * kCopies * 4;
+            fx = s64[lane * 4 + 0];
+            evt = s64[lane * 4 + 1];
+            N = s64[lane * 4 + 2];
+            nz = s64[lane * 4 + 3];
+        }
         {
+            constexpr int kBatch = 4;
             const unsigned* src = sums + (size_t)buf * kCopies * s5;
-            for (int j = tid; j < 5 * K; j += T) {
-                unsigned v[kCopies];
+            for (int j0 = tid; j0 < 5 * K; j0 += kBatch * T) {
+                unsigned v[kBatch][kCopies];
 #pragma unroll
-                for (int c = 0; c < kCopies; ++c) v[c] = src[(size_t)c * s5 + j];
-                unsigned t = 0;
-                if (j < 4 * K) {
+                for (int u = 0; u < kBatch; ++u) {
+                    const int j = j0 + u * T;
 #pragma unroll
-                    for (int c = 0; c < kCopies; ++c) t += v[c];
-                } else {
-#pragma unroll
-                    for (int c = 0; c < kCopies; ++c) t = max(t, v[c]);
+                    for (int c = 0; c < kCopies; ++c)
+                        v[u][c] = j < 5 * K ? src[(size_t)c * s5 + j] : 0u;
                 }
-                s_acc[j] = t;
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int j = j0 + u * T;
+                    if (j >= 5 * K) break;
+                    unsigned t = 0;
+                    if (j < 4 * K) {
+#pragma unroll
+                        for (int c = 0; c < kCopies; ++c) t += v[u][c];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < kCopies; ++c) t = max(t, v[u][c]);
+                    }
+                    s_acc[j] = t;
+                }
             }
         }
         if (wid == 0) {
-            const unsigned long long* s64 = sums64 + (size_t)buf * kCopies * 4;
-            unsigned long long fx = 0, evt = 0, N = 0, nz = 0;
-            if (lane < kCopies) {
-                fx = s64[lane * 4 + 0];
-                evt = s64[lane * 4 + 1];
-                N = s64[lane * 4 + 2];
-                nz = s64[lane * 4 + 3];
-            }
             fx = warp_sum_u64(fx);
             evt = warp_sum_u64(evt);
             N = warp_sum_u64(N);
