@@ -30,7 +30,7 @@ constexpr int kScanThreads = 512;
 constexpr int kScanWordsPerBlock = kScanWordsPerThread * kScanThreads;   // 2048
 constexpr int kScanBlocks = kMapWords / kScanWordsPerBlock;             // 256
 constexpr int kMaxTrace = 4096;              // SSE values kept per wsm_iterate call
-constexpr int kCopies = 4;                   // replicas of the global accumulators
+constexpr int kCopies = 1;                   // copies of the global accumulators
 constexpr int kChunk = 32;                   // colors per warp chunk (one per lane)
 constexpr int kMaxBatch = 64;                // images per persistent launch
 constexpr int kReduceSlots = 16;             // images per unique-color reduction launch

@@ -37,7 +37,7 @@
 //      sorted, so when the last of four is below the bound all four are
 //      visited.  Cluster sums (uint32, exact because an image has at most
 //      2^24 pixels) are accumulated per block in shared memory and added into
-//      one of kCopies replicated global accumulators (integer atomics: the
+//      the global accumulators (kCopies copies; integer atomics: the
 //      totals are exact and independent of the order).
 // The SSE is accumulated as an integer in units of 2^-20 (each color's
 // n_i * min_dist_i truncated to that grid), so every reduction is exact and
