@@ -454,8 +454,16 @@ WSM_API int wsm_set_grid_limit(wsm_handle* h, int blocks);
 /* Autotuner: runs the unique-color reduction of the batch once, then for
  * every resident shape `repeats` times the initialisation (untimed) and the
  * Sort-Means iterations (timed with CUDA events on `stream`), and makes the
- * fastest shape current.  Synchronises.  Items as for wsm_quantize_batch;
- * their centers and labels end as one complete run leaves them.
+ * fastest shape current.  Then, with that shape, it runs the iterations
+ * three more times to weigh the images: each image's group of blocks is
+ * timed on the device, and the image's share of the persistent launch's
+ * blocks is scaled by its time over the mean time, so that the groups end
+ * together.  The weights stay with the handle's image slots and apply to
+ * its later device-sized launches of the iterations (wsm_quantize_batch and
+ * its stages); they only move blocks between images, and every split gives
+ * the same results bit for bit.  Synchronises.  Items as for
+ * wsm_quantize_batch; their centers and labels end as one complete run
+ * leaves them.
  *   times_ms  host float [5] (may be NULL): best time of each shape, -1 if
  *             not resident
  * Returns the chosen shape (>= 0; with n_items = 0 the current one, nothing

@@ -270,7 +270,7 @@ void free_slots(wsm_handle* h) {
     void* ptrs[] = {h->tab,   h->tab_nb, h->sums,      h->sums64,   h->acc,       h->trace,
                     h->lut,   h->slot_ctrl, h->hist,   h->bitmap,   h->blk_total, h->batch_nu,
                     h->batch_mse, h->pick, h->plan, h->grid, h->bkt_count, h->bkt_cursor,
-                    h->keys16, h->bkt_work, h->bkt_nwork};
+                    h->keys16, h->bkt_work, h->bkt_nwork, h->slot_weight};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     void* host_ptrs[] = {h->host_nu, h->host_mse, h->host_pick};
@@ -288,6 +288,7 @@ void free_slots(wsm_handle* h) {
     h->batch_mse = nullptr;
     h->pick = nullptr;
     h->plan = nullptr;
+    h->slot_weight = nullptr;
     h->grid = nullptr;
     h->host_nu = nullptr;
     h->host_mse = nullptr;
@@ -334,6 +335,7 @@ int alloc_slots(wsm_handle* h, int slots) {
         {(void**)&h->batch_mse, sizeof(double) * n},
         {(void**)&h->pick, sizeof(uint32_t) * (size_t)h->max_K * n},
         {(void**)&h->plan, sizeof(int) * (n / kMaxBatch + 1) * (kMaxBatch + 1)},
+        {(void**)&h->slot_weight, sizeof(int) * n},
         {(void**)&h->grid, (size_t)kGridCells * n * h->label_bytes},
     };
     for (auto& a : allocs) {
@@ -364,6 +366,7 @@ int alloc_slots(wsm_handle* h, int slots) {
     if (e == cudaSuccess) e = cudaMemset(h->hist, 0, sizeof(uint32_t) * kHistBins * r);
     if (e == cudaSuccess) e = cudaMemset(h->bitmap, 0, sizeof(uint32_t) * kMapWords * r);
     if (e == cudaSuccess) e = cudaMemset(h->bkt_count, 0, sizeof(uint32_t) * kBuckets * r);
+    if (e == cudaSuccess) e = cudaMemset(h->slot_weight, 0, sizeof(int) * n);
     if (e == cudaSuccess)
         e = cudaMemset(h->acc, 0, sizeof(unsigned long long) * 4 * (size_t)h->max_K * n);
     if (e != cudaSuccess) {

@@ -68,6 +68,8 @@ struct Ctrl {
     double mse;                // host mirror slot of the last wsm_distortion
     unsigned long long map_sse;    // sum over colors of count * ||x - c||^2 in units of
                                    // 2^-20 (each term truncated) of the last final assignment
+    unsigned long long t_start;    // globaltimer at the start and the end of the slot's
+    unsigned long long t_end;      //   group in the last persistent launch of iterations
 };
 
 }  // namespace wsm
@@ -118,6 +120,8 @@ struct wsm_handle {
     double* batch_mse = nullptr;     // [slots] MSE of each image of the last wsm_distortion_batch
     uint32_t* pick = nullptr;        // [slots][max_K] initial center indices (wsm_init_batch)
     int* plan = nullptr;             // [slots / kMaxBatch + 1][kMaxBatch + 1] block splits
+    int* slot_weight = nullptr;      // [slots] work weight of each image in the device-side
+                                     //   split, 1/1024 units (0: 1), set by the autotuner
     int64_t* host_nu = nullptr;      // pinned mirrors of the three arrays above
     double* host_mse = nullptr;
     uint32_t* host_pick = nullptr;

@@ -92,6 +92,7 @@ struct BatchParams {
     const int64_t* n_dev;      // if set, image i has n_dev[item[i].slot] colors (written by an
                                //   earlier kernel) and the split is first_dev (k_plan)
     const int* first_dev;
+    const int* weight;         // with n_dev: per-slot work weights for the split (may be null)
     int cand_start;            // first pass of an iterate launch starts at the grid candidate
     int first_blk[kMaxBatch + 1];  // image i owns blocks [first_blk[i], first_blk[i+1])
     ItemDesc item[kMaxBatch];
@@ -222,8 +223,12 @@ __global__ void k_plan(const __grid_constant__ BatchParams P, int threads, int g
         for (size_t q = t; q < Z.n[r]; q += nt) Z.p[r][q] = 0u;
     if (t != 0) return;
     int64_t want[kMaxBatch];
-    for (int i = 0; i < P.n_items; ++i)
+    for (int i = 0; i < P.n_items; ++i) {
         want[i] = group_want(P.n_dev[P.item[i].slot], P.item[i].K, threads);
+        // a measured work weight (1/1024 units) scales the image's share
+        const int w = P.weight ? P.weight[P.item[i].slot] : 0;
+        if (w > 0) want[i] = max((int64_t)1, want[i] * w / 1024);
+    }
     split_groups(want, P.n_items, grid, first_dev);
 }
 
@@ -486,10 +491,13 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     // sizes from the device were checked by the initialisation, which flagged
     // an image with fewer unique colors than K; such an image is skipped
     // the caller's copies of N' and of the iterations run, at every exit
+    Ctrl* const gctrl = P.sc.ctrl + I.slot;
+    if (!kMap && b == 0 && threadIdx.x == 0) gctrl->t_start = global_ns();
     const auto outputs = [&](int iters) {
         if (!kMap && b == 0 && threadIdx.x == 0) {
             if (I.nu_out) *I.nu_out = n;
             if (I.iters_out) *I.iters_out = iters;
+            gctrl->t_end = global_ns();
         }
     };
     if (P.n_dev && n < K) {
@@ -892,7 +900,8 @@ static Scratch handle_scratch(wsm_handle* h) {
 // launched; otherwise the host splits the blocks.
 int launch_batch(const Scratch& sc, unsigned* status, bool map_mode, const ItemDesc* items,
                  int n_items, int max_iter, double eps, int threads, int grid_cap,
-                 const int64_t* n_dev, int* first_dev, bool cand_start, cudaStream_t s) {
+                 const int64_t* n_dev, int* first_dev, bool cand_start, cudaStream_t s,
+                 const int* weight = nullptr) {
     BatchParams P;
     P.sc = sc;
     P.status = status;
@@ -901,6 +910,7 @@ int launch_batch(const Scratch& sc, unsigned* status, bool map_mode, const ItemD
     P.eps = eps;
     P.n_dev = n_dev;
     P.first_dev = n_dev ? first_dev : nullptr;
+    P.weight = n_dev ? weight : nullptr;
     P.cand_start = cand_start ? 1 : 0;
     int64_t want[kMaxBatch];
     for (int i = 0; i < n_items; ++i) {
@@ -1003,7 +1013,7 @@ int iterate_items(wsm_handle* h, const wsm_item* items, int n_items, int max_ite
         int rc = launch_batch(handle_scratch(h), &h->ctrl->status, false, d, m, max_iter, eps,
                               kIterShapes[h->iter_shape].threads, iter_grid(h), n_dev,
                               h->plan + (size_t)(i0 / kMaxBatch) * (kMaxBatch + 1),
-                              h->cand_start, s);
+                              h->cand_start, s, h->slot_weight);
         if (rc != WSM_OK) return rc;
     }
     return WSM_OK;

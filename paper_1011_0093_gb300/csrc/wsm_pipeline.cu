@@ -214,6 +214,67 @@ extern "C" int wsm_launch_shape(wsm_handle* h, int shape, int* threads, int* blo
     return shape;
 }
 
+// Work weights of the images for the device-side block split (k_plan).  The
+// split gives each image blocks in proportion to its unique colors, but the
+// cost per color differs between images (visit lengths), and the launch
+// ends with its slowest image group.  Three rounds: run the iterations with
+// the current weights, read each group's time from the globaltimer stamps in
+// its control block, multiply each image's weight by its time over the mean
+// time (a slower group gets more blocks), and rescale so that the weighted
+// demand keeps its unweighted total.  Weights only move blocks between
+// images; every split gives the same results bit for bit.
+int calibrate_weights(wsm_handle* h, const wsm_item* items, int n_items, const uint64_t* seeds,
+                      int max_iter, double eps, cudaStream_t s) {
+    std::vector<double> w(n_items, 1.0);
+    cudaError_t e = cudaMemsetAsync(h->slot_weight, 0, sizeof(int) * n_items, s);
+    if (e != cudaSuccess) return cuda_fail(e, "weights reset");
+    if (n_items < 2) return WSM_OK;
+    std::vector<Ctrl> ctrl(n_items);
+    std::vector<int> wi(n_items);
+    std::vector<int64_t> nu(n_items);
+    for (int round = 0; round < 3; ++round) {
+        int rc = init_items_dev(h, items, n_items, seeds, s);
+        if (rc == WSM_OK) rc = iterate_items(h, items, n_items, max_iter, eps, h->batch_nu, s);
+        if (rc != WSM_OK) return rc;
+        e = cudaMemcpyAsync(ctrl.data(), h->slot_ctrl, sizeof(Ctrl) * n_items,
+                            cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(nu.data(), h->batch_nu, sizeof(int64_t) * n_items,
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "weights timing copy");
+        rc = read_status(h, s);
+        if (rc != WSM_OK) return rc;
+        double mean = 0.0;
+        int timed = 0;
+        for (int i = 0; i < n_items; ++i)
+            if (ctrl[i].t_end > ctrl[i].t_start) {
+                mean += (double)(ctrl[i].t_end - ctrl[i].t_start);
+                ++timed;
+            }
+        if (timed < 2) return WSM_OK;
+        mean /= timed;
+        double sum_old = 0.0, sum_new = 0.0;
+        for (int i = 0; i < n_items; ++i) {
+            const double base = (double)std::max<int64_t>(nu[i], 1);   // the demand's scale
+            sum_old += base;
+            if (ctrl[i].t_end > ctrl[i].t_start)
+                w[i] *= (double)(ctrl[i].t_end - ctrl[i].t_start) / mean;
+            w[i] = std::min(16.0, std::max(1.0 / 16.0, w[i]));
+            sum_new += base * w[i];
+        }
+        for (int i = 0; i < n_items; ++i) {
+            const double v = w[i] * sum_old / sum_new;
+            wi[i] = (int)std::min(16384.0, std::max(64.0, v * 1024.0 + 0.5));
+        }
+        e = cudaMemcpyAsync(h->slot_weight, wi.data(), sizeof(int) * n_items,
+                            cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "weights copy");
+    }
+    return WSM_OK;
+}
+
 extern "C" int wsm_autotune_batch(wsm_handle* h, const wsm_item* items, int n_items,
                                   const uint64_t* seeds, int max_iter, double eps, int repeats,
                                   float* times_ms, wsm_stream stream) {
@@ -271,6 +332,8 @@ extern "C" int wsm_autotune_batch(wsm_handle* h, const wsm_item* items, int n_it
         return rc != WSM_OK ? rc : fail(WSM_E_CUDA, "no launch shape could be timed");
     }
     h->iter_shape = best;
+    rc = calibrate_weights(h, items, n_items, seeds, max_iter, eps, s);
+    if (rc != WSM_OK) return rc;
     return best;
 }
 
