@@ -71,6 +71,7 @@ ITERS = 10
 N_IMAGES = 8
 H = W = 512
 METRIC = "unique-color assignments/s per iter (K=256) vs FP32 peak; 512² images/s end-to-end"
+WORKLOAD = "sweep 8x512x512 noise 0..24 (per GPU), K=256, WSM 10 iterations"
 UNIT = "assignments/s"
 L2_FLUSH_BYTES = 256 << 20
 # per step, all images together: hist24, scan_count, scan_emit (up to 16 images
@@ -255,10 +256,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "sweep 8x512x512 noise 0..24, K=256, WSM 10 iterations",
-                   "sample": "one whole image per step, cycling through the 8"},
+        "config": {"workload": WORKLOAD},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{nimg} whole images (one per step), single thread"},
+                         "sample": f"{nimg} whole images of the workload, one per step, cycling "
+                                   "through its 8 images, single thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -449,7 +450,7 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "sweep 8x512x512 noise 0..24 per GPU, K=256, WSM 10 iterations",
+            "config": {"workload": WORKLOAD,
                        "unique_colors": n_unique,
                        "images_per_step": len(images) * world,
                        "images_per_s": len(images) * world * args.steps / (total_ms * 1e-3),
