@@ -302,7 +302,14 @@ def run_gpu(args):
     wsm.wsm_set_first_pass_start(plan.handle, True)
     # the launch shape of the persistent kernel, picked by the library's
     # autotuner on these images (untimed)
-    best_shape, shape_ms = plan.tune(repeats=3)
+    if args.launch_shape >= 0:
+        # a fixed shape (profiling runs: under a profiler the autotuner's
+        # event timings include the profiler's own cost per launch)
+        wsm.wsm_set_launch_shape(plan.handle, args.launch_shape)
+        plan.weigh()
+        best_shape, shape_ms = args.launch_shape, None
+    else:
+        best_shape, shape_ms = plan.tune(repeats=3)
     shape = wsm.wsm_launch_shape(plan.handle, best_shape)[1:3]
     plan.run(wsm.STAGE_REDUCE | wsm.STAGE_INIT | wsm.STAGE_ITERATE)
     executed, _ = plan.stats()
@@ -1163,6 +1170,9 @@ def main():
     ap.add_argument("--lanes", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch-shape", type=int, default=-1,
+                    help="fix the persistent kernel's launch shape (index into the library's "
+                         "shapes; default: the autotuner picks it)")
     ap.add_argument("--no-hbm", action="store_true",
                     help="skip the HBM-bound stages on 4096x4096 images in the default form")
     args = ap.parse_args()

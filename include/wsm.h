@@ -473,6 +473,17 @@ WSM_API int wsm_autotune_batch(wsm_handle* h, const wsm_item* items, int n_items
                                const uint64_t* seeds, int max_iter, double eps, int repeats,
                                float* times_ms, wsm_stream stream);
 
+/* The second half of wsm_autotune_batch alone: with the handle's current
+ * launch shape (wsm_set_launch_shape), run the reduction once and the
+ * iterations three times, and set the images' work weights from the timed
+ * groups.  For a caller that fixes the shape itself.  Synchronises.  Items
+ * as for wsm_quantize_batch; their centers and labels end as one complete
+ * run leaves them.
+ * Errors: WSM_E_INVAL (items as for wsm_quantize_batch), WSM_E_TIMEOUT,
+ * WSM_E_CUDA. */
+WSM_API int wsm_weigh_batch(wsm_handle* h, const wsm_item* items, int n_items,
+                            const uint64_t* seeds, int max_iter, double eps, wsm_stream stream);
+
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of quantization requests (no counterpart in
  * the paper, which quantizes one image at a time).  A server owns `lanes`

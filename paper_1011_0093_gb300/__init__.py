@@ -20,7 +20,7 @@ from ._native import (MAX_K, MAX_K_WIDE, MAX_PIXELS, STAGE_ALL, STAGE_DISTORTION
                       wsm_quantize_batch, wsm_reduce, wsm_reduce_batch, wsm_reserve_batch,
                       wsm_measure_fp32, wsm_round_palette,
                       wsm_set_first_pass_start, wsm_set_grid_limit, wsm_set_launch_shape,
-                      wsm_set_reduce_path,
+                      wsm_set_reduce_path, wsm_weigh_batch,
                       wsm_sync_status)
 from .batch import BatchPlan
 from .serve import Server
@@ -40,7 +40,7 @@ __all__ = [
     "wsm_quantize_batch", "pipeline_items", "STAGE_REDUCE", "STAGE_INIT", "STAGE_ITERATE",
     "STAGE_MAP", "STAGE_INDEX", "STAGE_DISTORTION", "STAGE_ALL", "wsm_autotune_batch",
     "wsm_launch_shape", "wsm_set_launch_shape", "wsm_set_grid_limit", "wsm_set_first_pass_start",
-    "wsm_set_reduce_path",
+    "wsm_set_reduce_path", "wsm_weigh_batch",
     "wsm_batch_stats", "BatchPlan", "wsm_measure_fp32",
     # serving
     "Server",

@@ -100,6 +100,7 @@ SIGNATURES = {
     "wsm_server_stats_get": (C.c_int, [_P, C.POINTER(ServerStats)]),
     "wsm_server_destroy": (C.c_int, [_P]),
     "wsm_autotune_batch": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_double, C.c_int, _P, _P]),
+    "wsm_weigh_batch": (C.c_int, [_P, _P, C.c_int, _P, C.c_int, C.c_double, _P]),
     "wsm_distortion_fwd": (C.c_int, [_P, _P, C.c_int, _P, _I64, _P, C.c_int, C.c_int, _P,
                                      C.c_int, _P, _P, _P]),
     "wsm_distortion_bwd": (C.c_int, [_P, _P, C.c_int, _P, _I64, _P, C.c_int, C.c_int, _P, _P,
@@ -559,6 +560,15 @@ def wsm_autotune_batch(h: Handle, items, n_items: int, seeds, max_iter: int, eps
                                               int(repeats), C.cast(times, C.c_void_p),
                                               _stream(stream)))
     return q, [times[i] for i in range(N_SHAPES)]
+
+
+def wsm_weigh_batch(h: Handle, items, n_items: int, seeds, max_iter: int, eps: float,
+                    stream=None) -> None:
+    """Set the images' work weights for the handle's current launch shape."""
+    sd = seeds if isinstance(seeds, C.Array) else _seeds(seeds, n_items)
+    _check(lib().wsm_weigh_batch(h.ptr, C.cast(items, C.c_void_p), n_items,
+                                 C.cast(sd, C.c_void_p), int(max_iter), float(eps),
+                                 _stream(stream)))
 
 
 def wsm_batch_stats(h: Handle, n_items: int, stream=None) -> tuple[list[int], list[int]]:

@@ -145,6 +145,12 @@ class BatchPlan:
         return N.wsm_autotune_batch(self.handle, self._items, self.n_items, self._seeds,
                                     self.max_iter, self.eps, repeats)
 
+    def weigh(self):
+        """Weigh the loaded images for the current launch shape (the second
+        half of tune(), for a shape fixed with wsm_set_launch_shape)."""
+        N.wsm_weigh_batch(self.handle, self._items, self.n_items, self._seeds, self.max_iter,
+                          self.eps)
+
     def stats(self):
         """(distances evaluated, iterations) per image of the last persistent
         launch (after tune(): of the Sort-Means iterations)."""

@@ -275,6 +275,18 @@ int calibrate_weights(wsm_handle* h, const wsm_item* items, int n_items, const u
     return WSM_OK;
 }
 
+extern "C" int wsm_weigh_batch(wsm_handle* h, const wsm_item* items, int n_items,
+                               const uint64_t* seeds, int max_iter, double eps,
+                               wsm_stream stream) {
+    int rc = check_batch(h, items, n_items, seeds, max_iter);
+    if (rc != WSM_OK) return rc;
+    if (n_items == 0) return WSM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = reduce_items(h, items, n_items, s);
+    if (rc != WSM_OK) return rc;
+    return calibrate_weights(h, items, n_items, seeds, max_iter, eps, s);
+}
+
 extern "C" int wsm_autotune_batch(wsm_handle* h, const wsm_item* items, int n_items,
                                   const uint64_t* seeds, int max_iter, double eps, int repeats,
                                   float* times_ms, wsm_stream stream) {

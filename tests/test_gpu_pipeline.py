@@ -263,3 +263,27 @@ def test_packed_load_and_fetch_equal_per_image_copies(wsm):
         assert torch.equal(pal, ra["centers"].cpu())
         assert float(out["mse"][q]) == ra["mse"]
         assert torch.equal(b.images[q]["rgb"].cpu(), torch.from_numpy(img))
+
+
+def test_weighing_the_images_changes_no_result(wsm):
+    """wsm_weigh_batch (the image weights of the autotuner, for a fixed launch
+    shape) moves blocks between the images of a launch; every image's
+    results stay the same bit for bit."""
+    imgs = [synth.image(64 + 40 * q, 80 + 24 * q, 700 + q, 3 * q) for q in range(6)]
+    Ks = [16, 64, 32, 128, 48, 256]
+    seeds = [5 + q for q in range(6)]
+    plan = wsm.BatchPlan([i.shape for i in imgs], Ks, seeds, max_iter=8)
+    plan.load([torch.from_numpy(i) for i in imgs])
+    plan.run()
+    plan.sync()
+    before = [{k: (v.clone() if torch.is_tensor(v) else v) for k, v in plan.result(q).items()}
+              for q in range(len(imgs))]
+    wsm.wsm_set_launch_shape(plan.handle, 0)
+    plan.weigh()
+    plan.run()
+    plan.sync()
+    for q in range(len(imgs)):
+        r = plan.result(q)
+        assert torch.equal(r["centers"], before[q]["centers"])
+        assert torch.equal(r["index"], before[q]["index"])
+        assert r["mse"] == before[q]["mse"] and r["iters"] == before[q]["iters"]
