@@ -49,6 +49,7 @@
 #include <vector>
 
 #include "wsm_internal.cuh"
+#include "wsm_split.h"
 
 namespace wsm {
 
@@ -97,56 +98,6 @@ struct BatchParams {
     int first_blk[kMaxBatch + 1];  // image i owns blocks [first_blk[i], first_blk[i+1])
     ItemDesc item[kMaxBatch];
 };
-
-constexpr int64_t kGroupFloor = 16;   // blocks an image's group gets before the split
-
-// Blocks of one image's group: enough for every lane to hold a color and for
-// every warp to hold a table row.
-__host__ __device__ inline int64_t group_want(int64_t n, int K, int threads) {
-    const int64_t warps = threads / 32;
-    const int64_t for_colors = (n + threads - 1) / threads;
-    const int64_t for_rows = (K + warps - 1) / warps;
-    const int64_t w = for_colors > for_rows ? for_colors : for_rows;
-    return w > 1 ? w : 1;
-}
-
-// Split `grid` blocks into one group per image: min(want, floor) each, the
-// floor at most kGroupFloor and at most half of the grid over the images,
-// the rest in proportion to each image's want beyond that (every image gets
-// at least one; grid >= n_items), integer arithmetic only so that host and
-// device derive the same split.  Returns the number of blocks used.
-__host__ __device__ inline int split_groups(const int64_t* want, int n_items, int grid,
-                                            int* first_blk) {
-    int64_t total = 0;
-    for (int i = 0; i < n_items; ++i) total += want[i];
-    first_blk[0] = 0;
-    if (total <= grid) {
-        for (int i = 0; i < n_items; ++i) first_blk[i + 1] = first_blk[i] + (int)want[i];
-        return first_blk[n_items];
-    }
-    // every image first gets min(want, floor) blocks: a small image's group
-    // still has the warps for its row build and for the tail of its visits;
-    // the floors take at most half of the grid, so that with many images the
-    // large ones still get their share
-    const int64_t half = (int64_t)grid / (2 * n_items) > 1 ? (int64_t)grid / (2 * n_items) : 1;
-    const int64_t floor = half < kGroupFloor ? half : kGroupFloor;
-    int64_t fixed = 0;
-    for (int i = 0; i < n_items; ++i) fixed += want[i] < floor ? want[i] : floor;
-    const int64_t left = grid - fixed, excess = total - fixed;
-    int used = 0;
-    for (int i = 0; i < n_items; ++i) {
-        const int64_t f = want[i] < floor ? want[i] : floor;
-        first_blk[i + 1] = (int)(f + left * (want[i] - f) / excess);   // g_i, for now
-        used += first_blk[i + 1];
-    }
-    for (int i = 0; i < n_items && used < grid; ++i)   // the rounding remainder, in order
-        if (first_blk[i + 1] < want[i]) {
-            ++first_blk[i + 1];
-            ++used;
-        }
-    for (int i = 0; i < n_items; ++i) first_blk[i + 1] += first_blk[i];
-    return first_blk[n_items];
-}
 
 // floor(t / W) for t < 128 W (or t < 2^32 with a quotient below 2^8) and
 // 1 <= W <= 2^24: an FP32 estimate from the reciprocal, off by at most one,
@@ -224,10 +175,9 @@ __global__ void k_plan(const __grid_constant__ BatchParams P, int threads, int g
     if (t != 0) return;
     int64_t want[kMaxBatch];
     for (int i = 0; i < P.n_items; ++i) {
-        want[i] = group_want(P.n_dev[P.item[i].slot], P.item[i].K, threads);
         // a measured work weight (1/1024 units) scales the image's share
-        const int w = P.weight ? P.weight[P.item[i].slot] : 0;
-        if (w > 0) want[i] = max((int64_t)1, want[i] * w / 1024);
+        want[i] = weighted_want(group_want(P.n_dev[P.item[i].slot], P.item[i].K, threads),
+                                P.weight ? P.weight[P.item[i].slot] : 0);
     }
     split_groups(want, P.n_items, grid, first_dev);
 }
