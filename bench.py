@@ -122,7 +122,7 @@ def profiled_traffic():
     try:
         text = open(os.path.join(root, "profiles", "k_sortmeans_sweep8x512_K256.md")).read()
         src = b"".join(open(os.path.join(csrc, f), "rb").read()
-                       for f in ("wsm_iterate.cu", "wsm_internal.cuh"))
+                       for f in ("wsm_iterate.cu", "wsm_internal.cuh", "wsm_split.h"))
     except OSError:
         return None
     fields = dict(line.split(": ", 1) for line in text.splitlines()

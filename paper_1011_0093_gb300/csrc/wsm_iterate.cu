@@ -496,20 +496,54 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     Label* const grid = static_cast<Label*>(P.sc.grid) + (size_t)I.slot * kGridCells;
     const bool cand = !kMap && P.cand_start;
     if (cand) {
-        for (int c = b * T + tid; c < kGridCells; c += G * T) {
-            const float gx = (float)((c >> 8) * 16 + 8), gy = (float)(((c >> 4) & 15) * 16 + 8),
-                        gz = (float)((c & 15) * 16 + 8);
+        const int nt = G * T;
+        if (nt >= 2 * kGridCells) {
+            // `sub` consecutive lanes (2, 4 or 8) share a cell and scan every
+            // sub-th center; the reduction keeps the smaller distance and,
+            // between equal ones, the lower index, as the one-lane scan does.
+            // Every lane runs the shuffles (cells fill whole warps).
+            int sub = 2;
+            while (sub < 8 && nt >= 2 * sub * kGridCells) sub *= 2;
+            const int gt = b * T + tid, c = gt / sub, part = gt % sub;
             float bd = __int_as_float(0x7f800000);
             int bt = 0;
-            for (int k = 0; k < K; ++k) {
-                const float4 ck = s_c[k];
-                const float d = sq3(gx, gy, gz, ck.x, ck.y, ck.z);
-                if (d < bd) {
-                    bd = d;
-                    bt = k;
+            if (c < kGridCells) {
+                const float gx = (float)((c >> 8) * 16 + 8), gy = (float)(((c >> 4) & 15) * 16 + 8),
+                            gz = (float)((c & 15) * 16 + 8);
+                for (int k = part; k < K; k += sub) {
+                    const float4 ck = s_c[k];
+                    const float d = sq3(gx, gy, gz, ck.x, ck.y, ck.z);
+                    if (d < bd) {
+                        bd = d;
+                        bt = k;
+                    }
                 }
             }
-            grid[c] = (Label)bt;
+            for (int o = 1; o < sub; o <<= 1) {
+                const float od = __shfl_xor_sync(0xFFFFFFFFu, bd, o);
+                const int ot = __shfl_xor_sync(0xFFFFFFFFu, bt, o);
+                if (od < bd || (od == bd && ot < bt)) {
+                    bd = od;
+                    bt = ot;
+                }
+            }
+            if (c < kGridCells && part == 0) grid[c] = (Label)bt;
+        } else {
+            for (int c = b * T + tid; c < kGridCells; c += nt) {
+                const float gx = (float)((c >> 8) * 16 + 8), gy = (float)(((c >> 4) & 15) * 16 + 8),
+                            gz = (float)((c & 15) * 16 + 8);
+                float bd = __int_as_float(0x7f800000);
+                int bt = 0;
+                for (int k = 0; k < K; ++k) {
+                    const float4 ck = s_c[k];
+                    const float d = sq3(gx, gy, gz, ck.x, ck.y, ck.z);
+                    if (d < bd) {
+                        bd = d;
+                        bt = k;
+                    }
+                }
+                grid[c] = (Label)bt;
+            }
         }
         if (!grid_sync(&ctrl->bar_count, P.status, G)) return;
         // every block keeps a copy in shared memory for the first pass
