@@ -210,8 +210,8 @@ __device__ __forceinline__ CandResult candidate_search(float x, float y, float z
                                                     const float4* tab, const Label* tab_nb) {
     const float4 cq = s_c[q];
     const float dq = sq3(x, y, z, cq.x, cq.y, cq.z);
-    const float4* rq = tab + (size_t)q * K;
-    const Label* nq = tab_nb + (size_t)q * K;
+    const float4* rq = tab + q * K;
+    const Label* nq = tab_nb + q * K;
     int bpos = -1;                 // the best so far: c_p (-1), c_q (0) or entry bpos of row q
     float bmn = prev;
     if (dq <= prev) {              // c_q is later than c_p in row p
@@ -280,7 +280,7 @@ __device__ __forceinline__ CandResult candidate_search(float x, float y, float z
 // color's pruned visit of its row, and the per-block sums.  kCand: the first
 // pass of an iterate launch, whose search starts at the grid candidate.
 template <bool kMap, bool kCand, typename Label>
-__device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K, int G, int b,
+__device__ __forceinline__ void assign_pass(const ItemDesc& I, int n, int K, int G, int b,
                                             int WPB, int lane, int wid, unsigned* ticket,
                                             const float4* s_c, unsigned* s_acc, const float4* tab,
                                             const Label* tab_nb, const Label* grid, Label* lut,
@@ -293,13 +293,13 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
     // the group finish together whatever the cost of their colors.
     // per-lane counts of this pass fit 32 bits (at most 2^24 pixels per image)
     unsigned ev32 = 0, npix32 = 0, nz32 = 0;
-    int64_t cur = ((int64_t)b * WPB + wid) * kChunk;
-    int64_t nxt = n;
+    int cur = (b * WPB + wid) * kChunk;                 // colors: at most 2^24
+    int nxt = n;
     {
         unsigned t = 0;
         if (lane == 0 && cur < n) t = atomicAdd(ticket, 1u);
         t = __shfl_sync(0xFFFFFFFFu, t, 0);
-        if (cur < n) nxt = ((int64_t)G * WPB + t) * kChunk;
+        if (cur < n) nxt = (G * WPB + (int)t) * kChunk;
     }
     Label* const labels = static_cast<Label*>(I.labels);
     uint32_t col_n = 0, cnt_n = 0;
@@ -310,7 +310,7 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
         if (!kMap || I.counts) cnt_n = __ldg(I.counts + cur + lane);
     }
     while (cur < n) {
-        const int64_t i = cur + lane;
+        const int i = cur + lane;
         const bool active = i < n;
         const uint32_t col = col_n;
         const unsigned cnt = cnt_n;
@@ -363,7 +363,7 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
             }
         }
         if (scan_p) {
-            const float4* row = tab + (size_t)p * K;
+            const float4* row = tab + p * K;
             bool more = true;
             for (; more && j + 3 < K; j += 4) {
                 const float4 e0 = row[j], e1 = row[j + 1], e2 = row[j + 2], e3 = row[j + 3];
@@ -397,7 +397,7 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
                 WSM_VISIT(e, j);
             }
             ev32 += (unsigned)j;               // c_p plus the j - 1 visited centers
-            lab = mpos ? tab_nb[(size_t)p * K + mpos] : p;
+            lab = mpos ? tab_nb[p * K + mpos] : p;
         }
         if (active) {
             if (lab != p0) labels[i] = (Label)lab;
@@ -419,7 +419,7 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int64_t n, int K,
         }
         const unsigned t = __shfl_sync(0xFFFFFFFFu, t_after, 0);
         cur = nxt;
-        nxt = cur < n ? ((int64_t)G * WPB + t) * kChunk : n;
+        nxt = cur < n ? (G * WPB + (int)t) * kChunk : n;
     }
     ev += ev32;
     npix += npix32;
@@ -614,15 +614,15 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
         unsigned* const ticket = &ctrl->ticket[buf];
         if constexpr (!kMap) {
             if (cand && it == 0)
-                assign_pass<false, true, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc,
+                assign_pass<false, true, Label>(I, (int)n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc,
                                                 tab, tab_nb, s_grid, lut, sse_fx, ev, npix,
                                                 nonzero, bad);
             else
-                assign_pass<false, false, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc,
+                assign_pass<false, false, Label>(I, (int)n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc,
                                                  tab, tab_nb, s_grid, lut, sse_fx, ev, npix,
                                                  nonzero, bad);
         } else {
-            assign_pass<true, false, Label>(I, n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
+            assign_pass<true, false, Label>(I, (int)n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
                                             tab_nb, s_grid, lut, sse_fx, ev, npix, nonzero, bad);
         }
         if (bad) atomicOr(P.status, ST_BAD_LABEL);
