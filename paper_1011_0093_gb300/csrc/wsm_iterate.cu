@@ -38,7 +38,10 @@
 //      visited.  Cluster sums (uint32, exact because an image has at most
 //      2^24 pixels) are accumulated per block in shared memory and added into
 //      the global accumulators (kCopies copies; integer atomics: the
-//      totals are exact and independent of the order).
+//      totals are exact and independent of the order).  The first pass of a
+//      launch sums every color; later passes keep the totals and move only
+//      the colors whose membership changed from their old cluster to their
+//      new one.
 // The SSE is accumulated as an integer in units of 2^-20 (each color's
 // n_i * min_dist_i truncated to that grid), so every reduction is exact and
 // the results do not depend on the grid, the grouping or the order.
@@ -70,8 +73,10 @@ struct ItemDesc {
 struct Scratch {
     float4* tab;               // [max_K^2] rows of (d/4, c.x, c.y, c.z), nearest first
     void* tab_nb;              // [max_K^2] center index of each entry (label width)
-    unsigned* sums;            // [2][kCopies][5 max_K] cluster sums (4K) and the largest
-                               //   prev / min_dist of a member (K, FP32 bits), by pass parity
+    unsigned* sums;            // [2][kCopies][5 max_K] by pass parity: the largest prev /
+                               //   min_dist of a member (last K words, FP32 bits); the
+                               //   first 4K words of parity 0 hold the running cluster
+                               //   sums of the launch (those of parity 1 are unused)
     unsigned long long* sums64;    // [2][kCopies][4] SSE (2^-20 units), distances, pixels,
                                    //   colors with a nonzero minimum
     unsigned long long* acc;   // [4 max_K] cluster sums of the last pass
@@ -279,7 +284,17 @@ __device__ __forceinline__ CandResult candidate_search(float x, float y, float z
 // k_sortmeans): the warp's chunks of 32 colors, one color per lane, each
 // color's pruned visit of its row, and the per-block sums.  kCand: the first
 // pass of an iterate launch, whose search starts at the grid candidate.
-template <bool kMap, bool kCand, typename Label>
+// kDelta: the cluster sums of the previous pass are kept, so only a color
+// whose membership changes adds its terms, to its new cluster, and takes
+// them from its old one (the totals stay exact: integer sums).
+// Raises the shared word *a to v; a plain read first skips the atomic when the
+// word is already at least v (words only grow within a pass, so a stale read
+// can only cost an atomic, never lose a maximum).
+__device__ __forceinline__ void smem_max_u32(unsigned* a, unsigned v) {
+    if (v > *reinterpret_cast<volatile unsigned*>(a)) atomicMax(a, v);
+}
+
+template <bool kMap, bool kCand, bool kDelta, typename Label>
 __device__ __forceinline__ void assign_pass(const ItemDesc& I, int n, int K, int G, int b,
                                             int WPB, int lane, int wid, unsigned* ticket,
                                             const float4* s_c, unsigned* s_acc, const float4* tab,
@@ -407,11 +422,21 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int n, int K, int
                 // distance truncated to 2^-20 units as the per-pixel MSE does
                 sse_fx += (unsigned long long)cnt * sse_fixed(1u, mn);
             } else {
-                atomicAdd(s_acc + 4 * lab + 0, cnt * ((col >> 16) & 255u));
-                atomicAdd(s_acc + 4 * lab + 1, cnt * ((col >> 8) & 255u));
-                atomicAdd(s_acc + 4 * lab + 2, cnt * (col & 255u));
-                atomicAdd(s_acc + 4 * lab + 3, cnt);
-                atomicMax(s_acc + 4 * K + lab, __float_as_uint(mn));
+                if (!kDelta || lab != p) {
+                    const unsigned sr = cnt * ((col >> 16) & 255u), sg = cnt * ((col >> 8) & 255u),
+                                   sb = cnt * (col & 255u);
+                    atomicAdd(s_acc + 4 * lab + 0, sr);
+                    atomicAdd(s_acc + 4 * lab + 1, sg);
+                    atomicAdd(s_acc + 4 * lab + 2, sb);
+                    atomicAdd(s_acc + 4 * lab + 3, cnt);
+                    if (kDelta) {              // modulo 2^32: the totals are below 2^32
+                        atomicSub(s_acc + 4 * p + 0, sr);
+                        atomicSub(s_acc + 4 * p + 1, sg);
+                        atomicSub(s_acc + 4 * p + 2, sb);
+                        atomicSub(s_acc + 4 * p + 3, cnt);
+                    }
+                }
+                smem_max_u32(s_acc + 4 * K + lab, __float_as_uint(mn));
                 sse_fx += sse_fixed(cnt, mn);
                 npix32 += cnt;
                 nz32 += mn > 0.f;
@@ -572,13 +597,13 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
                             z = (float)(col & 255u);
                 const float4 cp = s_c[p];
                 const float prev = sq3(x, y, z, cp.x, cp.y, cp.z);
-                atomicMax(s_acc + 4 * K + p, __float_as_uint(prev));
+                smem_max_u32(s_acc + 4 * K + p, __float_as_uint(prev));
                 if (cand) {                        // the first pass also reads row q
                     const int q = s_grid[grid_cell(col)];
                     if (q != p) {
                         const float4 cq = s_c[q];
                         const float dq = sq3(x, y, z, cq.x, cq.y, cq.z);
-                        atomicMax(s_acc + 4 * K + q, __float_as_uint(dq));
+                        smem_max_u32(s_acc + 4 * K + q, __float_as_uint(dq));
                     }
                 }
             }
@@ -613,17 +638,22 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
         bool bad = false;
         unsigned* const ticket = &ctrl->ticket[buf];
         if constexpr (!kMap) {
-            if (cand && it == 0)
-                assign_pass<false, true, Label>(I, (int)n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc,
-                                                tab, tab_nb, s_grid, lut, sse_fx, ev, npix,
-                                                nonzero, bad);
+            if (it > 0)                        // the totals of the previous pass are kept
+                assign_pass<false, false, true, Label>(I, (int)n, K, G, b, WPB, lane, wid, ticket,
+                                                       s_c, s_acc, tab, tab_nb, s_grid, lut, sse_fx,
+                                                       ev, npix, nonzero, bad);
+            else if (cand)
+                assign_pass<false, true, false, Label>(I, (int)n, K, G, b, WPB, lane, wid, ticket,
+                                                       s_c, s_acc, tab, tab_nb, s_grid, lut, sse_fx,
+                                                       ev, npix, nonzero, bad);
             else
-                assign_pass<false, false, Label>(I, (int)n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc,
-                                                 tab, tab_nb, s_grid, lut, sse_fx, ev, npix,
-                                                 nonzero, bad);
+                assign_pass<false, false, false, Label>(I, (int)n, K, G, b, WPB, lane, wid, ticket,
+                                                        s_c, s_acc, tab, tab_nb, s_grid, lut, sse_fx,
+                                                        ev, npix, nonzero, bad);
         } else {
-            assign_pass<true, false, Label>(I, (int)n, K, G, b, WPB, lane, wid, ticket, s_c, s_acc, tab,
-                                            tab_nb, s_grid, lut, sse_fx, ev, npix, nonzero, bad);
+            assign_pass<true, false, false, Label>(I, (int)n, K, G, b, WPB, lane, wid, ticket, s_c,
+                                                   s_acc, tab, tab_nb, s_grid, lut, sse_fx, ev,
+                                                   npix, nonzero, bad);
         }
         if (bad) atomicOr(P.status, ST_BAD_LABEL);
         sse_fx = warp_sum_u64(sse_fx);
@@ -649,11 +679,14 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
         }
         if (kMap) break;
         {
+            // the block's changes of the running totals (parity 0 of its copy) and
+            // its maxima of the pass (this parity)
+            unsigned* tot = sums + (size_t)copy * s5;
             unsigned* dst = sums + (size_t)(buf * kCopies + copy) * s5;
             for (int j = tid; j < 5 * K; j += T) {
                 const unsigned v = s_acc[j];
                 if (v) {
-                    if (j < 4 * K) atomicAdd(dst + j, v);
+                    if (j < 4 * K) atomicAdd(tot + j, v);
                     else atomicMax(dst + j, v);
                 }
             }
@@ -675,6 +708,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
         }
         {
             constexpr int kBatch = 4;
+            // totals: parity 0 (kept across passes); maxima: this pass's parity
             const unsigned* src = sums + (size_t)buf * kCopies * s5;
             for (int j0 = tid; j0 < 5 * K; j0 += kBatch * T) {
                 unsigned v[kBatch][kCopies];
@@ -683,7 +717,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
                     const int j = j0 + u * T;
 #pragma unroll
                     for (int c = 0; c < kCopies; ++c)
-                        v[u][c] = j < 5 * K ? src[(size_t)c * s5 + j] : 0u;
+                        v[u][c] = j < 5 * K ? (j < 4 * K ? sums : src)[(size_t)c * s5 + j] : 0u;
                 }
 #pragma unroll
                 for (int u = 0; u < kBatch; ++u) {
@@ -726,11 +760,11 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
                 }
             }
         }
-        if (b == 0) {   // clear the accumulators of the next pass (read two barriers ago)
+        if (b == 0) {   // clear the maxima of the next pass (read two barriers ago)
             unsigned* nxt = sums + (size_t)(buf ^ 1) * kCopies * s5;
-            for (int j = tid; j < kCopies * 5 * K; j += T) {
-                const int c = j / (5 * K), r = j - c * 5 * K;
-                nxt[(size_t)c * s5 + r] = 0u;
+            for (int j = tid; j < kCopies * K; j += T) {
+                const int c = j / K, r = j - c * K;
+                nxt[(size_t)c * s5 + 4 * K + r] = 0u;
             }
             if (tid < 4 * kCopies) sums64[(size_t)(buf ^ 1) * kCopies * 4 + tid] = 0ull;
             if (tid == 0) ctrl->ticket[buf ^ 1] = 0u;   // drawn from two barriers ago
