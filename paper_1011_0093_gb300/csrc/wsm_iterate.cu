@@ -225,41 +225,35 @@ __device__ __forceinline__ CandResult candidate_search(float x, float y, float z
     }
     int v = 2;
     const auto center_at = [&](int pos) { return pos < 0 ? p : pos == 0 ? q : (int)nq[pos]; };
-    const auto visit = [&](const float4& e, int pos) {
+    // entry e at position pos of row q, when `in` (it is within the bound)
+    const auto visit = [&](const float4& e, int pos, bool in) {
         const float d = sq3(x, y, z, e.y, e.z, e.w);
-        ++v;
-        if (d < bmn) {
+        v += (int)in;
+        if (in && d < bmn) {
             bmn = d;
             bpos = pos;
-        } else if (d == bmn &&
+        } else if (in && d == bmn &&
                    key_in_row(s_c, p, center_at(pos)) > key_in_row(s_c, p, center_at(bpos))) {
             bpos = pos;
         }
     };
+    // rounds of four entries, the entries up to the bound being a prefix of
+    // the sorted row (as in the assignment pass)
     int j = 1;
     bool go = true;
     for (; go && j + 3 < K; j += 4) {
         const float4 e0 = rq[j], e1 = rq[j + 1], e2 = rq[j + 2], e3 = rq[j + 3];
-        if (e3.x <= dq) {
-            visit(e0, j);
-            visit(e1, j + 1);
-            visit(e2, j + 2);
-            visit(e3, j + 3);
-        } else {
-            go = false;
-            if (e0.x <= dq) {
-                visit(e0, j);
-                if (e1.x <= dq) {
-                    visit(e1, j + 1);
-                    if (e2.x <= dq) visit(e2, j + 2);
-                }
-            }
-        }
+        const bool v0 = e0.x <= dq, v1 = e1.x <= dq, v2 = e2.x <= dq, v3 = e3.x <= dq;
+        visit(e0, j, v0);
+        visit(e1, j + 1, v1);
+        visit(e2, j + 2, v2);
+        visit(e3, j + 3, v3);
+        go = v3;
     }
     for (; go && j < K; ++j) {
         const float4 e = rq[j];
         if (e.x > dq) break;
-        visit(e, j);
+        visit(e, j, true);
     }
     const int best = center_at(bpos);
     const float4 cp = s_c[p], cb = s_c[best];
@@ -275,6 +269,15 @@ __device__ __forceinline__ CandResult candidate_search(float x, float y, float z
     {                                                           \
         const float dist_ = sq3(x, y, z, (e).y, (e).z, (e).w);  \
         if (dist_ <= mn) {                                      \
+            mn = dist_;                                         \
+            mpos = (jj);                                        \
+        }                                                       \
+    }
+// The same for an entry of a round when `v` (the entry is below the bound).
+#define WSM_VISIT_IF(e, jj, v)                                  \
+    {                                                           \
+        const float dist_ = sq3(x, y, z, (e).y, (e).z, (e).w);  \
+        if ((v) && dist_ <= mn) {                               \
             mn = dist_;                                         \
             mpos = (jj);                                        \
         }                                                       \
@@ -380,29 +383,21 @@ __device__ __forceinline__ void assign_pass(const ItemDesc& I, int n, int K, int
         if (scan_p) {
             const float4* row = tab + p * K;
             bool more = true;
+            // Rounds of four entries.  A row is sorted, so the entries below the
+            // bound are a prefix of it: the visit stops within the first round
+            // whose last entry is not below it.  Every entry of a round has its
+            // distance computed and only those below the bound take part in the
+            // update, in row order, so a warp runs one path through a round.
             for (; more && j + 3 < K; j += 4) {
                 const float4 e0 = row[j], e1 = row[j + 1], e2 = row[j + 2], e3 = row[j + 3];
-                if (e3.x < prev) {
-                    WSM_VISIT(e0, j);
-                    WSM_VISIT(e1, j + 1);
-                    WSM_VISIT(e2, j + 2);
-                    WSM_VISIT(e3, j + 3);
-                } else {
+                const bool v0 = e0.x < prev, v1 = e1.x < prev, v2 = e2.x < prev, v3 = e3.x < prev;
+                WSM_VISIT_IF(e0, j, v0);
+                WSM_VISIT_IF(e1, j + 1, v1);
+                WSM_VISIT_IF(e2, j + 2, v2);
+                WSM_VISIT_IF(e3, j + 3, v3);
+                if (!v3) {                     // d[p][t] >= 4 prev_dist within this round: stop
+                    j += (int)v0 + (int)v1 + (int)v2;
                     more = false;
-                    if (e0.x < prev) {
-                        WSM_VISIT(e0, j);
-                        if (e1.x < prev) {
-                            WSM_VISIT(e1, j + 1);
-                            if (e2.x < prev) {
-                                WSM_VISIT(e2, j + 2);
-                                j += 3;
-                            } else {
-                                j += 2;
-                            }
-                        } else {
-                            j += 1;
-                        }
-                    }
                     break;
                 }
             }
@@ -807,6 +802,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     outputs(ctrl->iters_done);          // written by this thread in phase A
 }
 #undef WSM_VISIT
+#undef WSM_VISIT_IF
 
 // Dynamic shared memory of k_sortmeans for palettes of up to KM colors.
 static size_t sortmeans_smem(int KM, int threads, bool map_mode) {
