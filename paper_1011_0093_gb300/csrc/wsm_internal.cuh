@@ -258,6 +258,56 @@ __device__ __forceinline__ unsigned long long row_key(float d, int t, int p) {
     return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(t == p ? 0 : t + 1);
 }
 
+// Compare-exchange of a bitonic network step for the element held here
+// (index i) and its partner (index i ^ h, value o): the lower index of an
+// ascending block ((i & k) == 0) keeps the smaller key, of a descending one
+// the larger.
+__device__ __forceinline__ unsigned long long bitonic_keep(unsigned long long a,
+                                                           unsigned long long o, int i, int h,
+                                                           int k) {
+    const bool lower = (i & h) == 0, up = (i & k) == 0;
+    return (lower == up) ? (a < o ? a : o) : (a < o ? o : a);
+}
+
+// One step of the network between slots HS apart in the same lane (partners
+// 32 * HS elements apart): each pair once, from its lower slot.
+template <int HS>
+__device__ __forceinline__ void bitonic_slots(unsigned long long (&v)[8], int lane, int k) {
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        if (s & HS) continue;
+        const int t = s | HS;
+        const unsigned long long a = v[s], c = v[t];
+        const bool up = ((lane + 32 * s) & k) == 0;
+        const unsigned long long lo = a < c ? a : c, hi = a < c ? c : a;
+        v[s] = up ? lo : hi;
+        v[t] = up ? hi : lo;
+    }
+}
+
+// Sorts the 256 keys that one warp holds in registers, element lane + 32 s
+// in v[s], ascending (bitonic network; partners 32 or more apart are in the
+// same lane, nearer ones in lane ^ h).
+__device__ __forceinline__ void warp_bitonic256(unsigned long long (&v)[8], int lane) {
+    for (int k = 2; k <= 256; k <<= 1) {
+        for (int h = k >> 1; h > 0; h >>= 1) {
+            if (h == 128) {
+                bitonic_slots<4>(v, lane, k);
+            } else if (h == 64) {
+                bitonic_slots<2>(v, lane, k);
+            } else if (h == 32) {
+                bitonic_slots<1>(v, lane, k);
+            } else {
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, v[s], h);
+                    v[s] = bitonic_keep(v[s], o, lane + 32 * s, h, k);
+                }
+            }
+        }
+    }
+}
+
 // Barrier of the ts warps of team m (ts a power of two; a named barrier
 // 1 + m when ts > 1, so at most 15 teams of several warps per block).
 __device__ __forceinline__ void team_sync(int m, int ts) {
@@ -285,8 +335,10 @@ __device__ __forceinline__ int row_team_size(int K, int KM, int G, int WPB) {
 // d[p][t] < thr[p] (p itself always); the rank of a key among the kept keys
 // (keys are distinct, so the order in which they were collected does not
 // matter) is its entry position.  The team's threads split the comparisons
-// of a rank when there are more of them than kept keys.  Four entries with an
-// infinite bound follow the kept ones.
+// of a rank when there are more of them than kept keys; a row of more than
+// 128 kept keys built by a single warp is sorted in registers by a bitonic
+// network instead (the same order).  Four entries with an infinite bound
+// follow the kept ones.
 template <typename Label>
 __device__ __forceinline__ void build_rows(int K, int KM, int G, int b, const float4* s_c,
                                            const float* s_thr, unsigned long long* s_wkey,
@@ -323,6 +375,34 @@ __device__ __forceinline__ void build_rows(int K, int KM, int G, int b, const fl
         const int L = s_len[m];
         float4* row = tab + (size_t)p * K;
         Label* row_nb = tab_nb + (size_t)p * K;
+        if (ts == 1 && L > 128) {
+            // a long row kept by a single warp: sorted in registers by a
+            // bitonic network (the same order as the ranks below, keys being
+            // distinct), padded to 256 with keys above every real one
+            unsigned long long v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int j = lane + 32 * q;
+                v[q] = j < L ? key[j] : ~0ull;
+            }
+            warp_bitonic256(v, lane);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int j = lane + 32 * q;
+                if (j < L) {
+                    const unsigned lo = (unsigned)v[q];
+                    const int c = lo ? (int)lo - 1 : p;
+                    const float4 ct = s_c[c];
+                    const float d4 = __uint_as_float((unsigned)(v[q] >> 32)) * 0.25f;
+                    row[j] = make_float4(d4, ct.x, ct.y, ct.z);
+                    row_nb[j] = (Label)c;
+                }
+            }
+            if (r < 4 && L + r < K)
+                row[L + r] = make_float4(__int_as_float(0x7f800000), 0.f, 0.f, 0.f);
+            team_sync(m, ts);
+            continue;
+        }
         const int H = ts > 1 ? max(1, TT / L) : 1;               // threads per kept key
         if (H > 1) {
             for (int j = r; j < L; j += TT) rank_part[j] = 0;
