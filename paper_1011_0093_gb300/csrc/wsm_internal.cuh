@@ -271,10 +271,10 @@ __device__ __forceinline__ unsigned long long bitonic_keep(unsigned long long a,
 
 // One step of the network between slots HS apart in the same lane (partners
 // 32 * HS elements apart): each pair once, from its lower slot.
-template <int HS>
-__device__ __forceinline__ void bitonic_slots(unsigned long long (&v)[8], int lane, int k) {
+template <int HS, int S>
+__device__ __forceinline__ void bitonic_slots(unsigned long long (&v)[S], int lane, int k) {
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
+    for (int s = 0; s < S; ++s) {
         if (s & HS) continue;
         const int t = s | HS;
         const unsigned long long a = v[s], c = v[t];
@@ -285,27 +285,61 @@ __device__ __forceinline__ void bitonic_slots(unsigned long long (&v)[8], int la
     }
 }
 
-// Sorts the 256 keys that one warp holds in registers, element lane + 32 s
-// in v[s], ascending (bitonic network; partners 32 or more apart are in the
-// same lane, nearer ones in lane ^ h).
-__device__ __forceinline__ void warp_bitonic256(unsigned long long (&v)[8], int lane) {
-    for (int k = 2; k <= 256; k <<= 1) {
+// Sorts the 32 S keys (S = 4 or 8) that one warp holds in registers,
+// element lane + 32 s in v[s], ascending (bitonic network; partners 32 or
+// more apart are in the same lane, nearer ones in lane ^ h).
+template <int S>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[S], int lane) {
+    for (int k = 2; k <= 32 * S; k <<= 1) {
         for (int h = k >> 1; h > 0; h >>= 1) {
-            if (h == 128) {
-                bitonic_slots<4>(v, lane, k);
-            } else if (h == 64) {
-                bitonic_slots<2>(v, lane, k);
+            if constexpr (S == 8) {
+                if (h == 128) {
+                    bitonic_slots<4, 8>(v, lane, k);
+                    continue;
+                }
+            }
+            if (h == 64) {
+                bitonic_slots<2, S>(v, lane, k);
             } else if (h == 32) {
-                bitonic_slots<1>(v, lane, k);
+                bitonic_slots<1, S>(v, lane, k);
             } else {
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
+                for (int s = 0; s < S; ++s) {
                     const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, v[s], h);
                     v[s] = bitonic_keep(v[s], o, lane + 32 * s, h, k);
                 }
             }
         }
     }
+}
+
+// The L (<= 32 S) kept keys of row p, from shared memory, sorted by one warp
+// in registers and written as the row's entries, then its four sentinels.
+template <int S, typename Label>
+__device__ __forceinline__ void sort_row_in_registers(const unsigned long long* key, int L, int p,
+                                                      int K, int lane, const float4* s_c,
+                                                      float4* row, Label* row_nb) {
+    unsigned long long v[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        const int j = lane + 32 * q;
+        v[q] = j < L ? key[j] : ~0ull;
+    }
+    warp_bitonic<S>(v, lane);
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        const int j = lane + 32 * q;
+        if (j < L) {
+            const unsigned lo = (unsigned)v[q];
+            const int c = lo ? (int)lo - 1 : p;
+            const float4 ct = s_c[c];
+            const float d4 = __uint_as_float((unsigned)(v[q] >> 32)) * 0.25f;
+            row[j] = make_float4(d4, ct.x, ct.y, ct.z);
+            row_nb[j] = (Label)c;
+        }
+    }
+    if (lane < 4 && L + lane < K)
+        row[L + lane] = make_float4(__int_as_float(0x7f800000), 0.f, 0.f, 0.f);
 }
 
 // Barrier of the ts warps of team m (ts a power of two; a named barrier
@@ -336,7 +370,7 @@ __device__ __forceinline__ int row_team_size(int K, int KM, int G, int WPB) {
 // (keys are distinct, so the order in which they were collected does not
 // matter) is its entry position.  The team's threads split the comparisons
 // of a rank when there are more of them than kept keys; a row of more than
-// 128 kept keys built by a single warp is sorted in registers by a bitonic
+// 64 kept keys built by a single warp is sorted in registers by a bitonic
 // network instead (the same order).  Four entries with an infinite bound
 // follow the kept ones.
 template <typename Label>
@@ -375,31 +409,12 @@ __device__ __forceinline__ void build_rows(int K, int KM, int G, int b, const fl
         const int L = s_len[m];
         float4* row = tab + (size_t)p * K;
         Label* row_nb = tab_nb + (size_t)p * K;
-        if (ts == 1 && L > 128) {
+        if (ts == 1 && L > 64) {
             // a long row kept by a single warp: sorted in registers by a
             // bitonic network (the same order as the ranks below, keys being
-            // distinct), padded to 256 with keys above every real one
-            unsigned long long v[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int j = lane + 32 * q;
-                v[q] = j < L ? key[j] : ~0ull;
-            }
-            warp_bitonic256(v, lane);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int j = lane + 32 * q;
-                if (j < L) {
-                    const unsigned lo = (unsigned)v[q];
-                    const int c = lo ? (int)lo - 1 : p;
-                    const float4 ct = s_c[c];
-                    const float d4 = __uint_as_float((unsigned)(v[q] >> 32)) * 0.25f;
-                    row[j] = make_float4(d4, ct.x, ct.y, ct.z);
-                    row_nb[j] = (Label)c;
-                }
-            }
-            if (r < 4 && L + r < K)
-                row[L + r] = make_float4(__int_as_float(0x7f800000), 0.f, 0.f, 0.f);
+            // distinct), padded to 128 or 256 with keys above every real one
+            if (L > 128) sort_row_in_registers<8>(key, L, p, K, lane, s_c, row, row_nb);
+            else sort_row_in_registers<4>(key, L, p, K, lane, s_c, row, row_nb);
             team_sync(m, ts);
             continue;
         }
