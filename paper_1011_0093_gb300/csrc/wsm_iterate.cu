@@ -489,8 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
     const int T = blockDim.x, WPB = T >> 5;
     const int KM = P.sc.max_K;                  // smem arrays are sized for the batch's largest K
     float4* s_c = smem;                                                       // [KM] centers
-    float4* s_cn = s_c + KM;                                                  // [KM] new centers
-    unsigned* s_acc = reinterpret_cast<unsigned*>(s_cn + KM);                 // [5KM] sums, max
+    unsigned* s_acc = reinterpret_cast<unsigned*>(s_c + KM);                  // [5KM] sums, max
     float* s_thr = reinterpret_cast<float*>(s_acc + 5 * KM);                  // [KM] row bounds
     unsigned long long* s_wkey = reinterpret_cast<unsigned long long*>(s_thr + KM);
     // row keys: [WPB][KM], or [2 KM] for palettes of more than 256 colors
@@ -692,7 +691,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
         // Every load of the totals a thread needs is issued before any is
         // used: right after the barrier they come from L2 lines that all
         // blocks of the group have just updated, and a chain of dependent
-        // rounds of loads costs microseconds.
+        // rounds of loads costs microseconds.  The block's threads read the
+        // totals of their centers directly, so one block barrier ends the phase.
         unsigned long long fx = 0, evt = 0, N = 0, nz = 0;
         if (wid == 0 && lane < kCopies) {
             const unsigned long long* s64 = sums64 + (size_t)buf * kCopies * 4;
@@ -701,32 +701,53 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
             N = s64[lane * 4 + 2];
             nz = s64[lane * 4 + 3];
         }
+        if (b == 0) {   // clear the maxima of the next pass (read two barriers ago)
+            unsigned* nxt = sums + (size_t)(buf ^ 1) * kCopies * s5;
+            for (int j = tid; j < kCopies * K; j += T) {
+                const int c = j / K, r = j - c * K;
+                nxt[(size_t)c * s5 + 4 * K + r] = 0u;
+            }
+            if (tid < 4 * kCopies) sums64[(size_t)(buf ^ 1) * kCopies * 4 + tid] = 0ull;
+            if (tid == 0) ctrl->ticket[buf ^ 1] = 0u;   // drawn from two barriers ago
+        }
+        // One thread per center: its totals (the running sums and this pass's
+        // largest member distance), the new center c_k = S_k / W_k (an empty
+        // cluster keeps its center) and the bound of its next row.  A member x
+        // of cluster k had ||x - c_k|| <= sqrt(max_k) against the old center,
+        // so against the new one prev <= (sqrt(max_k) + ||c_k,new - c_k,old||)^2
+        // (triangle inequality); a visit of row k never goes past 4 prev.  The
+        // margin (x 1.001, + 1e-3) covers the FP32 rounding of these bounds.
         {
-            constexpr int kBatch = 4;
-            // totals: parity 0 (kept across passes); maxima: this pass's parity
-            const unsigned* src = sums + (size_t)buf * kCopies * s5;
-            for (int j0 = tid; j0 < 5 * K; j0 += kBatch * T) {
-                unsigned v[kBatch][kCopies];
+            const unsigned* mx = sums + (size_t)buf * kCopies * s5 + 4 * K;
+            for (int k = tid; k < K; k += T) {
+                unsigned v[5][kCopies];
 #pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
-                    const int j = j0 + u * T;
+                for (int c = 0; c < kCopies; ++c) {
 #pragma unroll
-                    for (int c = 0; c < kCopies; ++c)
-                        v[u][c] = j < 5 * K ? (j < 4 * K ? sums : src)[(size_t)c * s5 + j] : 0u;
+                    for (int q = 0; q < 4; ++q) v[q][c] = sums[(size_t)c * s5 + 4 * k + q];
+                    v[4][c] = mx[(size_t)c * s5 + k];
                 }
+                unsigned S[4] = {0u, 0u, 0u, 0u}, M = 0u;
 #pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
-                    const int j = j0 + u * T;
-                    if (j >= 5 * K) break;
-                    unsigned t = 0;
-                    if (j < 4 * K) {
+                for (int c = 0; c < kCopies; ++c) {
 #pragma unroll
-                        for (int c = 0; c < kCopies; ++c) t += v[u][c];
-                    } else {
+                    for (int q = 0; q < 4; ++q) S[q] += v[q][c];
+                    M = max(M, v[4][c]);
+                }
+                const float4 o = s_c[k];
+                float4 cn = make_float4(o.x, o.y, o.z, 0.f);
+                if (S[3]) {
+                    const float rcp = __frcp_rn((float)S[3]);
+                    cn.x = div_rn_u32(S[0], S[3], rcp);
+                    cn.y = div_rn_u32(S[1], S[3], rcp);
+                    cn.z = div_rn_u32(S[2], S[3], rcp);
+                }
+                const float r = sqrtf(__uint_as_float(M)) + sqrtf(sq3(o.x, o.y, o.z, cn.x, cn.y, cn.z));
+                s_thr[k] = 4.f * (r * r * 1.001f + 1e-3f);
+                s_c[k] = cn;
+                if (b == 0) {
 #pragma unroll
-                        for (int c = 0; c < kCopies; ++c) t = max(t, v[u][c]);
-                    }
-                    s_acc[j] = t;
+                    for (int q = 0; q < 4; ++q) acc[4 * k + q] = S[q];
                 }
             }
         }
@@ -755,41 +776,6 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
                 }
             }
         }
-        if (b == 0) {   // clear the maxima of the next pass (read two barriers ago)
-            unsigned* nxt = sums + (size_t)(buf ^ 1) * kCopies * s5;
-            for (int j = tid; j < kCopies * K; j += T) {
-                const int c = j / K, r = j - c * K;
-                nxt[(size_t)c * s5 + 4 * K + r] = 0u;
-            }
-            if (tid < 4 * kCopies) sums64[(size_t)(buf ^ 1) * kCopies * 4 + tid] = 0ull;
-            if (tid == 0) ctrl->ticket[buf ^ 1] = 0u;   // drawn from two barriers ago
-        }
-        __syncthreads();
-        {
-            const float* s_cf = reinterpret_cast<const float*>(s_c);
-            float* s_cnf = reinterpret_cast<float*>(s_cn);
-            for (int u = tid; u < 3 * K; u += T) {
-                const int k = u / 3, ch = u - 3 * k;
-                const unsigned w = s_acc[4 * k + 3];
-                s_cnf[4 * k + ch] = w ? div_rn_u32(s_acc[4 * k + ch], w, __frcp_rn((float)w))
-                                      : s_cf[4 * k + ch];
-            }
-            if (b == 0)
-                for (int j = tid; j < 4 * K; j += T) acc[j] = s_acc[j];
-        }
-        __syncthreads();
-        // Row bound for the next pass: a member x of cluster k had
-        // ||x - c_k|| <= sqrt(max_k) against the old center, so against the new
-        // one prev <= (sqrt(max_k) + ||c_k,new - c_k,old||)^2 (triangle
-        // inequality); a visit of row k never goes past 4 prev.  The margin
-        // (x 1.001, + 1e-3) covers the FP32 rounding of these bounds.
-        for (int k = tid; k < K; k += T) {
-            const float4 o = s_c[k], c = s_cn[k];
-            const float r = sqrtf(__uint_as_float(s_acc[4 * K + k])) +
-                            sqrtf(sq3(o.x, o.y, o.z, c.x, c.y, c.z));
-            s_thr[k] = 4.f * (r * r * 1.001f + 1e-3f);
-            s_c[k] = make_float4(c.x, c.y, c.z, 0.f);
-        }
         __syncthreads();
         if (s_stop) break;
         build_rows<Label>(K, KM, G, b, s_c, s_thr, s_wkey, tab, tab_nb);
@@ -809,7 +795,7 @@ static size_t sortmeans_smem(int KM, int threads, bool map_mode) {
     const size_t keys = KM > WSM_MAX_K ? (size_t)2 * KM : (size_t)(threads / 32) * KM;
     // the candidate grid of the first pass (iterations only)
     const size_t grid = map_mode ? 0 : (size_t)kGridCells * (KM > WSM_MAX_K ? 2 : 1);
-    return (size_t)KM * (16 + 16 + 20 + 4) + keys * 8 + grid;
+    return (size_t)KM * (16 + 20 + 4) + keys * 8 + grid;
 }
 
 // The launch shapes of the persistent kernel: threads per block and blocks
