@@ -181,12 +181,14 @@ def test_visits_and_counts_follow_algorithm_2_without_the_candidate_start(wsm, h
 
 
 @pytest.mark.parametrize("paper_scan", [False, True])
-@pytest.mark.parametrize("s,K", [(1, 256), (4, 64), (6, 32)])
+@pytest.mark.parametrize("s,K", [(1, 256), (4, 64), (6, 32), (2, 200), (5, 100)])
 def test_exact_arithmetic_every_membership_and_count(wsm, h, s, K, paper_scan):
     """Passes from centers on the 1/8 grid, where FP32 and FP64 compute every
     distance exactly: every membership, exact ties included, must be the one
     Algorithm 2's visit order gives (the later of equal distances), and with
-    the paper's start the distance count must be Algorithm 2's."""
+    the paper's start the distance count must be Algorithm 2's.  Palettes of
+    100 and 200 colors give rows of 65..128 and 129..200 kept entries, whose
+    sort pads the keys to 128 and 256."""
     flips = teacher_forced(wsm, h, synth.sweep_512_one(s), K, 40 + s, 6, paper_scan=paper_scan,
                            exact=True)
     assert flips == 0
