@@ -455,7 +455,7 @@ WSM_API int wsm_set_grid_limit(wsm_handle* h, int blocks);
  * every resident shape `repeats` times the initialisation (untimed) and the
  * Sort-Means iterations (timed with CUDA events on `stream`), and makes the
  * fastest shape current.  Then, with that shape, it runs the iterations
- * three more times to weigh the images: each image's group of blocks is
+ * six more times to weigh the images: each image's group of blocks is
  * timed on the device, and the image's share of the persistent launch's
  * blocks is scaled by its time over the mean time, so that the groups end
  * together.  The weights stay with the handle's image slots and apply to
@@ -475,7 +475,7 @@ WSM_API int wsm_autotune_batch(wsm_handle* h, const wsm_item* items, int n_items
 
 /* The second half of wsm_autotune_batch alone: with the handle's current
  * launch shape (wsm_set_launch_shape), run the reduction once and the
- * iterations three times, and set the images' work weights from the timed
+ * iterations six times, and set the images' work weights from the timed
  * groups.  For a caller that fixes the shape itself.  Synchronises.  Items
  * as for wsm_quantize_batch; their centers and labels end as one complete
  * run leaves them.
