@@ -220,19 +220,21 @@ __global__ void __launch_bounds__(kBuckets) k_bkt_plan(const __grid_constant__ R
 // array with one global atomic, and the threads write the staged keys' low
 // 14 bits to consecutive positions of those ranges.  The per-bucket tables
 // are indexed by bslot.
-constexpr int kScatterThreads = 256;
-constexpr int kScatterPix = kScatterThreads * kGroup;      // 4096 pixels per tile
+constexpr int kScatterThreads = 512;    // tiles of 8192 pixels: 0.409 -> 0.400 ms for
+                                          // 4 x 4096^2 against 4096 (16384: 0.411)
+constexpr int kScatterPerSM = 1024 / kScatterThreads;      // resident blocks per SM
+constexpr int kScatterPix = kScatterThreads * kGroup;      // pixels per tile
 constexpr int kScatterPer = kBuckets / kScatterThreads;    // buckets per thread in the scan
 static_assert(kBuckets % kScatterThreads == 0, "the tile scan splits the buckets evenly");
 
-__global__ void __launch_bounds__(kScatterThreads, 4)
+__global__ void __launch_bounds__(kScatterThreads, kScatterPerSM)
     k_bkt_scatter(const __grid_constant__ ReduceItems R) {
     __shared__ unsigned s_cnt[kBuckets];      // pixels of each bucket in the tile
     __shared__ unsigned s_base[kBuckets];     // their offset within the tile
     __shared__ unsigned s_gpos[kBuckets];     // their first position in the key array
     __shared__ unsigned s_w[kScatterThreads / 32];
     __shared__ unsigned s_total;
-    __shared__ uint32_t s_key[kScatterPix];
+    extern __shared__ uint32_t s_key[];       // [kScatterPix] the tile's keys in bucket order
     const int i = item_of_block(R.first_blk, R.n_items, blockIdx.x);
     const int g = blockIdx.x - R.first_blk[i], G = R.first_blk[i + 1] - R.first_blk[i];
     const uint8_t* rgb = R.rgb[i];
@@ -574,11 +576,14 @@ static int launch_reduce(wsm_handle* h, ReduceItems& R, cudaStream_t s) {
         split_pixels(R, (int64_t)h->sms * 8, [](int64_t n) { return (n + 4095) / 4096; });
         if (R.first_blk[R.n_items] > 0) k_bkt_count<<<R.first_blk[R.n_items], 256, 0, s>>>(R);
         k_bkt_plan<<<R.n_items, kBuckets, 0, s>>>(R);
-        // scatter pass: at most 4 blocks of 256 per SM in all, tiles of 4096 pixels
-        split_pixels(R, (int64_t)h->sms * 4,
+        // scatter pass: the resident blocks of every SM at most, tiles of kScatterPix pixels
+        e = raise_smem_limit((const void*)k_bkt_scatter, kScatterPix * sizeof(uint32_t));
+        if (e != cudaSuccess) return cuda_fail(e, "scatter set-up");
+        split_pixels(R, (int64_t)h->sms * kScatterPerSM,
                      [](int64_t n) { return (n + kScatterPix - 1) / kScatterPix; });
         if (R.first_blk[R.n_items] > 0)
-            k_bkt_scatter<<<R.first_blk[R.n_items], kScatterThreads, 0, s>>>(R);
+            k_bkt_scatter<<<R.first_blk[R.n_items], kScatterThreads,
+                            kScatterPix * sizeof(uint32_t), s>>>(R);
         k_bkt_hist<<<h->sms * 3, kBktHistThreads, kBktBins * sizeof(unsigned), s>>>(
             R, (int)bkt_max_work(nmax));
     } else {
