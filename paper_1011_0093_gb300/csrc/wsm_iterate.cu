@@ -9,11 +9,12 @@
 // counts share one launch.  Within a group:
 //   0  bound pass: every color's squared distance to its current center,
 //      prev = ||x - c_p||^2, raises the largest prev of cluster p;
-//   A  block b of the group (of G) turns the cluster sums of the previous
-//      pass into the new centers c_k = S_k / W_k (correctly rounded to FP32;
-//      an empty cluster keeps its center), measures that pass's SSE and
-//      applies the Sec. 3.2 stop rule (all blocks compute the same values,
-//      so all decide alike); then teams of warps of the group's blocks
+//   A  every block of the group turns the cluster sums of the previous pass
+//      into the new centers c_k = S_k / W_k, one thread per center
+//      (correctly rounded to FP32; an empty cluster keeps its center),
+//      measures that pass's SSE and applies the Sec. 3.2 stop rule (all
+//      blocks compute the same values, so all decide alike); then teams of
+//      warps of the group's blocks
 //      build the rows of the center table: row p lists, nearest first, the
 //      entries (d[p][t] / 4, c_t), ties ordered by (t != p, t), so entry 0
 //      is p.
@@ -33,9 +34,10 @@
 //      with d[p][t] / 4 >= prev (the paper's d[p][t] >= 4 prev_dist; scaling
 //      by 4 is exact), and a visited center replaces the current one when its
 //      distance is <= the running minimum, so among equal distances the one
-//      visited last wins.  Entries are loaded four at a time; a row is
-//      sorted, so when the last of four is below the bound all four are
-//      visited.  Cluster sums (uint32, exact because an image has at most
+//      visited last wins.  Entries are loaded four at a time and all four
+//      distances computed; a row is sorted, so the entries below the bound
+//      are a prefix of it, and only those take part in the update, in row
+//      order.  Cluster sums (uint32, exact because an image has at most
 //      2^24 pixels) are accumulated per block in shared memory and added into
 //      the global accumulators (kCopies copies; integer atomics: the
 //      totals are exact and independent of the order).  The first pass of a
