@@ -11,6 +11,8 @@ compared GPU pass from the oracle's state, so one rounding decision cannot
 carry over; whole runs are compared free-running until the first such
 decision and in teacher forcing after it.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -426,6 +428,32 @@ def test_max_iter_zero_keeps_centers(wsm, h):
     before = centers.clone()
     done, trace = wsm.wsm_iterate(h, colors, counts, nu, 8, centers, labels, 0, 0.0)
     assert done == 0 and trace == [] and torch.equal(centers[:, :3], before[:, :3])
+
+
+def test_empty_cluster_keeps_its_center_and_sse_is_taken_before_the_update(wsm, h):
+    """The oracle's hand-worked pin (test_oracle_pins) through the C ABI: one
+    pass from memberships 0, 0, 0 gives 0, 1, 1; nothing joins the third
+    center, which keeps its place (reading R3); the second becomes the FP32
+    rounding of 56/5; the pass's SSE is the assignment step's, 5/6 (reading
+    R4; every distance is an integer here, so the fixed-point SSE is exact)."""
+    colors = torch.tensor([0x000000, 0x0A0000, 0x0C0000], dtype=torch.uint32, device="cuda")
+    counts = torch.tensor([1, 2, 3], dtype=torch.uint32, device="cuda")
+    centers = torch.tensor([[0, 0, 0, 0], [11, 0, 0, 0], [200, 200, 200, 0]],
+                           dtype=torch.float32, device="cuda")
+    labels = torch.zeros(3, dtype=torch.uint8, device="cuda")
+    for first_pass_start in (True, False):
+        c, lab = centers.clone(), labels.clone()
+        wsm.wsm_set_first_pass_start(h, first_pass_start)
+        try:
+            done, trace = wsm.wsm_iterate(h, colors, counts, 3, 3, c, lab, 1, 0.0)
+        finally:
+            wsm.wsm_set_first_pass_start(h, True)
+        assert done == 1
+        assert lab.cpu().tolist() == [0, 1, 1]
+        assert c[:, :3].cpu().tolist() == [[0.0, 0.0, 0.0],
+                                           [float(np.float32(56 / 5)), 0.0, 0.0],
+                                           [200.0, 200.0, 200.0]]
+        assert math.isclose(trace[0], 5 / 6, rel_tol=1e-15)
 
 
 def test_bad_labels_and_indices_reported(wsm, h):

@@ -24,6 +24,7 @@ PIN_CALLS = [
     ("exhaustive minimum", lambda: pins.test_assign_finds_exhaustive_minimum_from_any_start(5)),
     ("exact fractions", pins.test_update_matches_exact_fractions),
     ("K=1 closed form", pins.test_k1_closed_form),
+    ("empty cluster and SSE step", pins.test_empty_cluster_keeps_its_center_and_sse_is_taken_before_the_update),
     ("K=N' lossless", pins.test_k_equals_unique_count_is_lossless),
     ("weighted == batch", pins.test_weighted_equals_batch_kmeans),
     ("monotone + termination", pins.test_sse_never_increases_and_termination_rule),
@@ -71,6 +72,18 @@ MUTANTS = [
      "index[p] = (uint8_t)labels[at];"),
     ("palette index range check admits K", "if (k < 0 || k >= K) return -1.0;",
      "if (k < 0 || k > K) return -1.0;"),
+    ("empty cluster moved to the origin",
+     "        if (W[k] > 0)\n            for (int c = 0; c < 3; ++c) centers[3 * k + c] = (double)S[3 * k + c] / (double)W[k];",
+     "        for (int c = 0; c < 3; ++c)\n            centers[3 * k + c] = W[k] > 0 ? (double)S[3 * k + c] / (double)W[k] : 0.0;"),
+    ("SSE measured after the update instead of at the assignment step",
+     "        sse = 0.0;\n        for (int64_t i = 0; i < n_unique; ++i) sse += ((double)counts[i] / N) * mind[i];\n"
+     "        wsmo_update(colors, counts, n_unique, labels, K, centers, S_, W_);",
+     "        wsmo_update(colors, counts, n_unique, labels, K, centers, S_, W_);\n        sse = 0.0;\n"
+     "        for (int64_t i = 0; i < n_unique; ++i) {\n            double x[3], e = 0.0;\n"
+     "            unpack(colors[i], x);\n"
+     "            for (int c = 0; c < 3; ++c) {\n"
+     "                const double t = x[c] - centers[3 * labels[i] + c];\n                e += t * t;\n            }\n"
+     "            sse += ((double)counts[i] / N) * e;\n        }"),
 ]
 
 

@@ -261,6 +261,29 @@ def test_k1_closed_form():
     assert math.isclose(r["sse_trace"][1], float(var), rel_tol=1e-12)
 
 
+def test_empty_cluster_keeps_its_center_and_sse_is_taken_before_the_update():
+    """Worked by hand.  Colors (0,0,0) x1, (10,0,0) x2, (12,0,0) x3; centers
+    c0 = (0,0,0), c1 = (11,0,0), c2 = (200,200,200); every color starts in
+    cluster 0.  Row 0 is c0, c1 (d = 121), c2 (d = 120000).  (0,0,0): prev = 0,
+    the visit stops at once.  (10,0,0): prev = 100, 121 < 400 so c1 is visited
+    at distance 1 and taken; 120000 >= 400 stops.  (12,0,0): prev = 144, c1 at
+    distance 1.  So the memberships are 0, 1, 1; nothing joins c2, which keeps
+    its place (reading R3); c0 = (0,0,0), c1 = ((2*10 + 3*12) / 5, 0, 0) =
+    (11.2, 0, 0).  The SSE of the assignment step (reading R4) is
+    (1*0 + 2*1 + 3*1) / 6 = 5/6; measured after the update it would be
+    (2*1.2^2 + 3*0.8^2) / 6 = 0.8."""
+    colors = np.array([0x000000, 0x0A0000, 0x0C0000], np.uint32)
+    counts = np.array([1, 2, 3], np.uint32)
+    centers = np.array([[0.0, 0.0, 0.0], [11.0, 0.0, 0.0], [200.0, 200.0, 200.0]])
+    r = oracle.iteration(colors, counts, centers, np.zeros(3, np.int32))
+    assert list(r["labels"]) == [0, 1, 1]
+    assert list(r["W"]) == [1, 5, 0]
+    assert r["centers"][2].tolist() == [200.0, 200.0, 200.0]
+    assert r["centers"][0].tolist() == [0.0, 0.0, 0.0]
+    assert r["centers"][1].tolist() == [56 / 5, 0.0, 0.0]
+    assert math.isclose(r["sse"], 5 / 6, rel_tol=1e-15)    # FP64 sum of w_i * d_i
+
+
 def test_k_equals_unique_count_is_lossless():
     img = synth.tiny(8, 8, 2, 3)
     colors, counts = oracle.unique(img)
