@@ -17,6 +17,7 @@ PIN_CALLS = [
     ("splitmix64 vector", pins.test_splitmix64_published_vector),
     ("init valid", pins.test_init_indices_valid),
     ("init uniform", pins.test_init_subsets_uniform),
+    ("init on the published stream", pins.test_init_floyd_on_the_published_stream),
     ("init centers", pins.test_init_centers_are_the_drawn_colors),
     ("center distances", pins.test_center_distances_closed_form),
     ("row sort", pins.test_sort_rows_order_and_ties),
@@ -84,6 +85,9 @@ MUTANTS = [
      "            for (int c = 0; c < 3; ++c) {\n"
      "                const double t = x[c] - centers[3 * labels[i] + c];\n                e += t * t;\n            }\n"
      "            sse += ((double)counts[i] / N) * e;\n        }"),
+    ("Floyd step draws with the candidate top as the counter",
+     "uint64_t t = wsmo_splitmix64(seed, (uint64_t)taken) % (uint64_t)(j + 1);",
+     "uint64_t t = wsmo_splitmix64(seed, (uint64_t)j) % (uint64_t)(j + 1);"),
 ]
 
 

@@ -104,6 +104,22 @@ def test_init_subsets_uniform():
     assert chi2 < 45.0      # 14 degrees of freedom: p < 1e-4 beyond this
 
 
+def test_init_floyd_on_the_published_stream():
+    """Step r of Floyd's sample (Bentley & Floyd 1987) reduces draw r of the
+    seed's stream, which for seed 0 is the published splitmix64 output r
+    (tests/golden/splitmix64.txt): t = draw_r mod (j + 1) for j = n - K + r,
+    taken unless already taken, else j.  The sizes are ones where a draw
+    repeats an earlier pick at the second or the third step."""
+    draws = [int(v, 16) for seed, _, v in read_golden("splitmix64.txt") if seed == "0"]
+    K = len(draws)
+    for n in (3, 7, 8, 13, 22, 32, 1000):
+        picks = []
+        for r, j in enumerate(range(n - K, n)):
+            t = draws[r] % (j + 1)
+            picks.append(j if t in picks else t)
+        assert oracle.init_indices(n, K, 0).tolist() == sorted(picks), n
+
+
 def test_init_centers_are_the_drawn_colors():
     colors = tiny_colors(3, 40, 6)
     c0, lab = oracle.init(colors, 7, 123)
